@@ -1,0 +1,360 @@
+"""Throughput benchmark of the fused DDF lattice Boltzmann step on GB300.
+
+One benchmark step = one run of the throughput workload: ``--lb-steps`` fused
+time steps of a Taylor-Green lattice pair (flow + scalar, D2Q9 each) followed by
+the local strain-rate / vorticity fields of the final state.  Prints one JSON
+line (rank 0).  ``--impl reference`` times the FP64 CPU checker on a bounded
+sample of the same workload instead.
+
+Launch: ``python bench.py [--gpus N --steps K --warmup W]``; for N > 1 under
+torch.distributed.run, every rank advances its own lattice (replicas, weak
+scaling) and the slowest rank's time counts.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DDF-LB MLUPS with local ω/S, % of HBM peak; surrogate steps-to-steady saved"
+BYTES_PER_CELL = {"fp32": 144, "fp16": 72, "bf16": 72}  # 18 populations read + written
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=16384, help="grid side of the Taylor-Green lattice")
+    ap.add_argument("--lb-steps", type=int, default=200, help="fused time steps per benchmark step")
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = str(device_index)
+        try:  # nvidia-smi numbering can differ from CUDA's: select by PCI bus id
+            import torch
+            pr = torch.cuda.get_device_properties(device_index)
+            self.idx = f"{pr.pci_domain_id:08X}:{pr.pci_bus_id:02X}:{pr.pci_device_id:02X}.0"
+        except Exception:
+            pass
+        self.proc = None
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.tmp.name)
+        if not rows:
+            return None
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = max((float(r[2]) for r in rows if r[2].replace(".", "").isdigit()), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, v: float) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64,
+                     device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rates(nu):
+    w = 1.0 / (3.0 * nu + 0.5)  # nu = c_s^2 (1/omega - 1/2), c_s^2 = 1/3
+    return (0, 0, 0, 1.2, w, w, 1.2, 1.2, 1.2), (0, w, w, 1.2, 1.2, 1.2, 1.2, 1.2, 1.2)
+
+
+def workload_name(args):
+    return (f"taylor-green {args.n}x{args.n}, D2Q9 flow + scalar, {args.storage} storage, "
+            f"{args.lb_steps} fused steps + local S/omega fields per benchmark step")
+
+
+# ------------------------------------------------------------------ CPU checker
+def cpu_sample(seconds: float = 12.0, n: int = 1024, lb_per_call: int = 2):
+    """Time the FP64 checker on Taylor-Green n^2 (the sweep's error-reference
+    size) for about ``seconds``: returns (MLUPS, cores, description)."""
+    import oracle as O
+    from paper_1908_06742_gb300 import inputs
+    cores = O.threads(os.cpu_count() or 1)
+    wf, wg = rates(0.01)
+    F = inputs.taylor_green(n, 0.01, phi_amp=0.1)
+    L = O.OracleLattice(O.OracleParams(nx=n, ny=n, lam_override=wf, lam_phi_override=wg))
+    L.init(F.rho, F.ux, F.uy, F.phi, F.grads)
+    L.step(1)
+    done, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        L.step(lb_per_call)
+        done += lb_per_call
+    L.fields()
+    dt = time.perf_counter() - t0
+    return n * n * done / dt / 1e6, cores, f"FP64 checker, taylor-green {n}x{n}, {done} steps + fields, {dt:.1f} s"
+
+
+def run_reference(args, world, rank):
+    """The reference arm: the FP64 CPU checker on a bounded sample per step."""
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_1908_06742_gb300 import inputs
+    cores = O.threads(os.cpu_count() or 1)
+    n, lb = 1024, 4
+    wf, wg = rates(0.01)
+    F = inputs.taylor_green(n, 0.01, phi_amp=0.1)
+    L = O.OracleLattice(O.OracleParams(nx=n, ny=n, lam_override=wf, lam_phi_override=wg))
+    L.init(F.rho, F.ux, F.uy, F.phi, F.grads)
+    for _ in range(args.warmup):
+        L.step(lb); L.fields()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        L.step(lb); L.fields()
+    dt = time.perf_counter() - t0
+    v = n * n * lb * args.steps / dt / 1e6
+    sample = f"FP64 checker, taylor-green {n}x{n}, {lb} steps + fields per benchmark step"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(args), "sample": sample},
+        "cpu_baseline": {"value": round(v, 3), "unit": "MLUPS", "cores": cores,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(v, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }))
+
+
+# ------------------------------------------------------------------ GPU arm
+def traffic_per_launch(args, n_cells):
+    """DRAM bytes per k_step launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        from paper_1908_06742_gb300 import build as B
+        import hashlib
+        h = hashlib.sha256()
+        for s in sorted(os.listdir(B.CSRC)):
+            with open(os.path.join(B.CSRC, s), "rb") as fh:
+                h.update(fh.read())
+        e = d.get(f"k_step_{args.storage}")
+        if not e or e.get("source_sha256") != h.hexdigest():
+            return None
+        return e["dram_bytes_per_cell"] * n_cells
+    except Exception:
+        return None
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_1908_06742_gb300 import build as B
+    from paper_1908_06742_gb300 import ddflb as D
+    from paper_1908_06742_gb300 import inputs
+
+    B.build()
+    D.load()
+    dev = torch.device("cuda", local)
+    n, lb = args.n, args.lb_steps
+    wf, wg = rates(0.01)
+    cfg = D.Config(nx=n, ny=n, storage=args.storage, omega_f=wf, omega_g=wg,
+                   scale_f=2.0 ** 10 if args.storage == "fp16" else 0.0,
+                   scale_g=2.0 ** 10 if args.storage == "fp16" else 0.0,
+                   host_io=not args.no_e2e)
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        lat = D.Lattice(cfg, device=dev, stream=stream)
+        T = inputs.taylor_green(n, 0.01, phi_amp=0.1, xp=torch, device=dev)
+        f32 = [a.float() for a in (T.rho, T.ux, T.uy, T.phi, T.grads)]
+        del T
+        lat.init(*f32)
+        outs = {k: torch.empty((n, n), dtype=torch.float32, device=dev) for k in D.FIELD_NAMES}
+        fptrs = [outs[k].data_ptr() for k in D.FIELD_NAMES]
+        lib = lat.lib
+
+        def bench_step():
+            D._check(lib.ddflb_step(lat._h, lb))
+            D._check(lib.ddflb_fields(lat._h, *fptrs))
+
+        for _ in range(args.warmup):
+            bench_step()
+        stream.synchronize()
+
+        # timed region: K benchmark steps, events on the launching stream
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+               torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        clocks = ClockSampler(local)
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        clocks.start()
+        t_host = time.perf_counter()
+        for a, b, c in ev:
+            a.record(stream)
+            D._check(lib.ddflb_step(lat._h, lb))
+            b.record(stream)
+            D._check(lib.ddflb_fields(lat._h, *fptrs))
+            c.record(stream)
+        torch.cuda.synchronize(dev)
+        t_host = time.perf_counter() - t_host
+        barrier(world)
+        clk = clocks.stop()
+        total_ms = sum(a.elapsed_time(c) for a, _, c in ev)
+        step_ms = sum(a.elapsed_time(b) for a, b, _ in ev)
+        total_ms = max_over_ranks(world, total_ms)
+        launches = args.steps * (lb + 1)
+
+        cells = n * n
+        value = world * cells * lb * args.steps / (total_ms / 1e3) / 1e6
+        kernel_s = step_ms / 1e3 / (lb * args.steps)     # average k_step launch duration
+        algo_bytes = BYTES_PER_CELL[args.storage] * cells
+        peak, kind = peaks()
+        achieved = algo_bytes / kernel_s / 1e9
+        stats = lat.stats()
+
+        # end to end through the C ABI with host buffers: copy in, init, steps, fields out
+        e2e = None
+        if not args.no_e2e:
+            pin = lambda t: t.cpu().pin_memory()
+            h_in = [pin(a) for a in f32]
+            h_out = {k: torch.empty((n, n), dtype=torch.float32).pin_memory()
+                     for k in D.FIELD_NAMES}
+            del f32
+            e2e_steps = max(1, min(args.steps, 3))
+            lat.init_host(*h_in).step(lb)
+            lat.fields_host(h_out)
+            barrier(world)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            for _ in range(e2e_steps):
+                lat.init_host(*h_in)
+                lat.step(lb)
+                lat.fields_host(h_out)
+            torch.cuda.synchronize(dev)
+            dt = max_over_ranks(world, time.perf_counter() - t0)
+            e2e = {"value": round(world * cells * lb * e2e_steps / dt / 1e6, 1), "unit": "MLUPS",
+                   "h2d_bytes_per_step": int(sum(a.numel() * 4 for a in h_in)),
+                   "d2h_bytes_per_step": int(8 * cells * 4), "steps": e2e_steps}
+
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu:
+        v, cores, sample = cpu_sample()
+        cpu = {"value": round(v, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+               "sample": sample}
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_name(args), "grid": n, "lb_steps_per_step": lb,
+                   "storage": args.storage, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": f"inputs larger than L2 ({2 * algo_bytes / 2 / 1e9:.1f} GB of populations per copy)",
+                   "hbm_pct": round(100 * achieved / peak, 1)},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_kind": kind,
+                     "kernel": "k_step", "algorithmic_bytes_per_launch": algo_bytes,
+                     "traffic": traffic_per_launch(args, cells)},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "host_wall_s": round(t_host, 3),
+        "checks": {"mass": stats["mass"], "diverged": stats["diverged"]},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,179 @@
+/*
+ * ddflb.h - C ABI of the GB300 (sm_103a) double-distribution-function lattice
+ * Boltzmann library with local vorticity recovery.
+ *
+ * Method: Hajabdollahi & Premnath, "Local vorticity computation in double
+ * distribution functions based lattice Boltzmann methods for flow and scalar
+ * transport", arXiv 1908.06742.  Two D2Q9 lattices advance together: the flow
+ * populations f with the MRT collision of Sec. 2 (Eq. MRT-LBEfluidmotion_transformed,
+ * body force F = 0) and the passive-scalar populations g with the MRT collision
+ * of Sec. 3 (Eq. MRT-LBECDE), whose third-order off-diagonal equilibria carry
+ * the anisotropy beta1 != beta2 (Eq. eqmrawmoment_CDE).  The strain rate S_ij
+ * and the vorticity omega_z are recovered node by node from the second-order
+ * non-equilibrium moments of both lattices (Sec. 4, Eqs. crossderivativeRHS1 to
+ * vorticityexpression), with no finite differences.
+ *
+ * Conventions for every entry point:
+ *  - Units are lattice units, dx = dt = 1 (Sec. 5).  Node (i, j) is at x = i,
+ *    y = j; fields are row-major [ny][nx] float arrays, x fastest.
+ *  - Pointers named dev_* or documented as device pointers must be CUDA device
+ *    memory of the current device.  The library never allocates device memory:
+ *    the caller owns the workspace and every field buffer, and must keep them
+ *    alive until ddflb_destroy / ddflb_batch_destroy.
+ *  - Calls are asynchronous on the stream given at creation, except the *_stats
+ *    calls, which synchronise that stream.
+ *  - Errors are returned as ddflb_status, never thrown; a message describing
+ *    the last error of the calling thread is available from ddflb_last_error().
+ *  - Time: the state after n calls-worth of steps is the PRE-collision state
+ *    f(x, t = n), g(x, t = n); ddflb_fields reports the fields of that state.
+ */
+#ifndef DDFLB_H
+#define DDFLB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DDFLB_OK = 0,
+  DDFLB_EINVAL = 1,         /* invalid argument or parameter */
+  DDFLB_ENOMEM = 2,         /* workspace smaller than *_workspace_bytes() */
+  DDFLB_ECUDA = 3,          /* a CUDA runtime call failed (message has the CUDA error) */
+  DDFLB_EDIVERGED = 4,      /* a reduction found a non-finite mass or scalar sum */
+  DDFLB_ENOTCONVERGED = 5,  /* a run-to-tolerance call stopped at its step limit */
+  DDFLB_ETIMEOUT = 6        /* a device-side wait gave up after its spin limit */
+} ddflb_status;
+
+/* Boundary kinds (Sec. 5).  Walls are half-way bounce-back for f (Sec. 5.1,
+ * 5.4); the moving wall adds the momentum term 2 w_a rho0 (e_a . u_w) / c_s^2;
+ * the scalar takes a fixed value on walls by anti-bounce-back
+ * g_a = -g*_abar + 2 w_a phi_w (the paper fixes the value, not the scheme). */
+typedef enum {
+  DDFLB_BC_PERIODIC = 0, /* periodic in x and y (Sec. 5.2)                          */
+  DDFLB_BC_CAVITY = 1,   /* walls on all sides; top wall (above row ny-1) moves with
+                            (u_lid, 0) and holds phi_lid, others hold phi_wall (5.4) */
+  DDFLB_BC_CHANNEL = 2   /* periodic in x; static bottom wall with phi_wall, top wall
+                            moving with (u_lid, 0) holding phi_lid (Sec. 5.1, 5.3)   */
+} ddflb_bc;
+
+/* Storage precision of the populations.  Populations are stored as deviations
+ * from the rest equilibrium, (f_a - w_a rho0) * scale_f and (g_a - w_a phi0) *
+ * scale_g; collision arithmetic is always FP32. */
+typedef enum { DDFLB_FP32 = 0, DDFLB_FP16 = 1, DDFLB_BF16 = 2 } ddflb_storage;
+
+/* ddflb_params.flags */
+#define DDFLB_FLAG_HOST_IO 1 /* reserve a staging area so ddflb_init_host /
+                                ddflb_fields_host can take host buffers */
+
+typedef struct {
+  int32_t nx, ny;       /* grid size, each >= 2 (channel: nx >= 1)                */
+  int32_t bc;           /* ddflb_bc                                               */
+  int32_t storage;      /* ddflb_storage                                          */
+  /* Relaxation diagonals in the non-orthogonal basis of Eq. (basisvectors):
+   * omega_f = diag(0,0,0,w3,w4,w5,w6,w7,w8) of Eq. (relaxationtimematrix_fluidmotion),
+   * nu = cs2 (1/w4 - 1/2) with w4 = w5; omega_g = diag(0,w1^phi..w8^phi) of
+   * Eq. (relaxationtimematrix_CDE), D_phi = cs2_phi (1/w1^phi - 1/2).  Entries
+   * 0..2 of omega_f and entry 0 of omega_g must be 0 (conserved moments). Every
+   * rate must lie in [0, 2]. */
+  double omega_f[9];
+  double omega_g[9];
+  double beta1, beta2;  /* scalar-flux anisotropy, |beta1 - beta2| > 1e-6 (Sec. 4) */
+  double cs2, cs2_phi;  /* c_s^2 and c_sphi^2 (1/3 in the paper)                   */
+  double rho0, phi0;    /* rest state: storage offsets; rho0 also in the lid term   */
+  double u_lid;         /* x velocity of the moving wall (cavity, channel)          */
+  double phi_lid;       /* scalar value held by the moving wall                     */
+  double phi_wall;      /* scalar value held by the other walls                     */
+  double phi_min;       /* where |phi| < phi_min the cross derivatives and omega
+                           are written as NaN (Sec. 4 requires phi != 0)            */
+  double scale_f, scale_g; /* storage scale (power of two; <= 0 means 1)           */
+  int32_t check_every;  /* steps between reductions in ddflb_step (0 = none)        */
+  int32_t flags;        /* DDFLB_FLAG_*                                             */
+} ddflb_params;
+
+typedef struct ddflb_ctx ddflb_ctx;
+
+/* Bytes of device workspace ddflb_create needs for these parameters (0 if the
+ * parameters are invalid; see ddflb_last_error). */
+size_t ddflb_workspace_bytes(const ddflb_params* p);
+
+/* Validate *p, carve the population buffers, reduction scratch and status
+ * block out of dev_workspace (device memory of at least
+ * ddflb_workspace_bytes(p) bytes, 256-byte aligned), and bind cuda_stream
+ * (a cudaStream_t; NULL = legacy default stream).  Host memory for the handle
+ * is the only allocation.  Errors: EINVAL (parameters, alignment, NULL),
+ * ENOMEM (bytes too small). */
+ddflb_status ddflb_create(const ddflb_params* p, void* dev_workspace, size_t bytes,
+                          void* cuda_stream, ddflb_ctx** out);
+
+/* Set the state at t = 0 from macroscopic device fields rho, ux, uy, phi
+ * ([ny][nx] floats each) and optional gradients grads (6 planes [6][ny][nx]:
+ * d_x u_x, d_y u_x, d_x u_y, d_y u_y, d_x phi, d_y phi; NULL = equilibrium).
+ * The populations are the equilibria of Eqs. (eqmrawmoment), (eqmrawmoment_CDE)
+ * plus the Chapman-Enskog non-equilibrium parts of Eqs. (strainratexxpyy) to
+ * (strainratexy) and (1stnoneqmmomentx_CDE), (1stnoneqmmomenty_CDE),
+ * (offdiagonal2ndnoneqmmoment_CDE).  Resets the step counter and status. */
+ddflb_status ddflb_init(ddflb_ctx* c, const float* rho, const float* ux, const float* uy,
+                        const float* phi, const float* grads);
+
+/* ddflb_init with HOST input buffers (same layout); the copies run on the
+ * context stream through the staging area, so the host buffers must stay
+ * valid until the stream reaches this point (pinned memory for overlap).
+ * Requires DDFLB_FLAG_HOST_IO at creation (else EINVAL). */
+ddflb_status ddflb_init_host(ddflb_ctx* c, const float* rho, const float* ux, const float* uy,
+                             const float* phi, const float* grads);
+
+/* Advance n >= 0 time steps: one fused pass per step streams f and g (pull),
+ * applies the wall rules, collides both lattices in moment space and stores the
+ * post-collision deviations.  Every check_every steps a reduction records the
+ * mass, scalar and velocity residual r = |u(t)-u(t-1)|_2 / |u(t)|_2 (FP64
+ * sums) in the device status block; once a sum is non-finite further steps are
+ * skipped and the next ddflb_stats returns EDIVERGED. */
+ddflb_status ddflb_step(ddflb_ctx* c, int64_t n);
+
+/* Local kinematics of the current state (Sec. 4): density, velocity, scalar,
+ * S_xx = d_x u_x, S_xy = (d_x u_y + d_y u_x)/2, S_yy = d_y u_y and
+ * omega_z = d_x u_y - d_y u_x, each into a [ny][nx] device float buffer.  Any
+ * pointer may be NULL to skip that field. */
+ddflb_status ddflb_fields(ddflb_ctx* c, float* rho, float* ux, float* uy, float* phi,
+                          float* sxx, float* sxy, float* syy, float* omega);
+
+/* ddflb_fields into HOST buffers (staged; requires DDFLB_FLAG_HOST_IO).  The
+ * copies are queued on the context stream; the call synchronises it before
+ * returning so the host buffers hold the result. */
+ddflb_status ddflb_fields_host(ddflb_ctx* c, float* rho, float* ux, float* uy, float* phi,
+                               float* sxx, float* sxy, float* syy, float* omega);
+
+/* The pre-collision populations of the current state as full values (not
+ * deviations), f and g each [9][ny][nx] device floats (either may be NULL). */
+ddflb_status ddflb_populations(ddflb_ctx* c, float* f, float* g);
+
+/* Reduce the current state now and return (synchronising the stream): total
+ * mass sum rho, total scalar sum phi, the residual of the last check (NaN if
+ * none yet) and the number of steps taken.  Any output pointer may be NULL.
+ * Returns EDIVERGED once a non-finite sum has been seen. */
+ddflb_status ddflb_stats(ddflb_ctx* c, double* mass, double* scalar, double* residual,
+                         int64_t* step);
+
+/* Checkpoint: size in bytes of the raw state, and copies of it to/from a
+ * caller device buffer (device-to-device, asynchronous).  Resuming from a saved
+ * state reproduces the run bit for bit. */
+size_t ddflb_state_bytes(const ddflb_ctx* c);
+ddflb_status ddflb_get_state(ddflb_ctx* c, void* dev_dst, size_t bytes, int64_t* step);
+ddflb_status ddflb_set_state(ddflb_ctx* c, const void* dev_src, size_t bytes, int64_t step);
+
+/* Release the handle (host memory only; the workspace stays the caller's). */
+ddflb_status ddflb_destroy(ddflb_ctx* c);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* ddflb_last_error(void);
+
+/* Library version string. */
+const char* ddflb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DDFLB_H */

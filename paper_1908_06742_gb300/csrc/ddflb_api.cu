@@ -1,0 +1,399 @@
+// C ABI of the DDF lattice Boltzmann library (declared in include/ddflb.h).
+//
+// Host-side runtime: parameter validation, workspace carving (the caller owns
+// all device memory), the step loop with its periodic reductions, host-staged
+// I/O, checkpoints and thread-local error messages.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/ddflb.h"
+#include "ddflb_internal.h"
+
+using namespace ddflb;
+
+namespace {
+
+thread_local std::string g_err;
+
+ddflb_status fail(ddflb_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+ddflb_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(DDFLB_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+size_t elem_size(int storage) { return storage == DDFLB_FP32 ? 4 : 2; }
+
+struct Layout {
+  int pitch;
+  size_t pops_bytes;  // one buffer: 2 lattices x 9 planes
+  size_t off_a, off_b, off_uprev, off_part, off_status, off_stage, total;
+};
+
+// Row pitch: a multiple of 64 elements keeps every row start 128-byte aligned
+// for 16-bit storage and 256-byte aligned for FP32.
+Layout layout(const ddflb_params* p) {
+  Layout L{};
+  L.pitch = (int)align_up((size_t)p->nx, 64);
+  const size_t plane = (size_t)L.pitch * p->ny;
+  const size_t cells = (size_t)p->nx * p->ny;
+  L.pops_bytes = align_up(2 * 9 * plane * elem_size(p->storage), kAlign);
+  size_t o = 0;
+  L.off_a = o; o += L.pops_bytes;
+  L.off_b = o; o += L.pops_bytes;
+  L.off_uprev = o; o += align_up(2 * cells * sizeof(float), kAlign);
+  L.off_part = o; o += align_up((size_t)kReduceBlocks * 4 * sizeof(double), kAlign);
+  L.off_status = o; o += align_up(sizeof(DevStatus), kAlign);
+  L.off_stage = o;
+  if (p->flags & DDFLB_FLAG_HOST_IO) o += align_up(10 * cells * sizeof(float), kAlign);
+  L.total = o;
+  return L;
+}
+
+ddflb_status validate(const ddflb_params* p) {
+  if (!p) return fail(DDFLB_EINVAL, "params is NULL");
+  if (p->bc < 0 || p->bc > 2) return fail(DDFLB_EINVAL, "bc %d is not a ddflb_bc", p->bc);
+  const int minx = p->bc == DDFLB_BC_CHANNEL ? 1 : 2;
+  if (p->nx < minx || p->ny < 2) return fail(DDFLB_EINVAL, "grid %d x %d too small", p->nx, p->ny);
+  if ((int64_t)p->nx * p->ny > (int64_t)1 << 32)
+    return fail(DDFLB_EINVAL, "grid %d x %d exceeds 2^32 nodes", p->nx, p->ny);
+  if (p->storage < 0 || p->storage > 2) return fail(DDFLB_EINVAL, "storage %d invalid", p->storage);
+  for (int k = 0; k < 9; ++k) {
+    if (!(p->omega_f[k] >= 0.0 && p->omega_f[k] <= 2.0))
+      return fail(DDFLB_EINVAL, "omega_f[%d] = %g outside [0, 2]", k, p->omega_f[k]);
+    if (!(p->omega_g[k] >= 0.0 && p->omega_g[k] <= 2.0))
+      return fail(DDFLB_EINVAL, "omega_g[%d] = %g outside [0, 2]", k, p->omega_g[k]);
+  }
+  if (p->omega_f[0] != 0 || p->omega_f[1] != 0 || p->omega_f[2] != 0)
+    return fail(DDFLB_EINVAL, "omega_f[0..2] must be 0 (mass and momentum are conserved)");
+  if (p->omega_g[0] != 0) return fail(DDFLB_EINVAL, "omega_g[0] must be 0 (phi is conserved)");
+  if (!(std::fabs(p->beta1 - p->beta2) > 1e-6))
+    return fail(DDFLB_EINVAL, "beta1 - beta2 = %g: the vorticity needs beta1 != beta2",
+                p->beta1 - p->beta2);
+  if (!(p->cs2 > 0 && p->cs2 < 1) || !(p->cs2_phi > 0 && p->cs2_phi < 1))
+    return fail(DDFLB_EINVAL, "cs2, cs2_phi must lie in (0, 1)");
+  if (!std::isfinite(p->rho0) || p->rho0 <= 0) return fail(DDFLB_EINVAL, "rho0 must be > 0");
+  if (!std::isfinite(p->phi0) || !std::isfinite(p->u_lid) || !std::isfinite(p->phi_lid) ||
+      !std::isfinite(p->phi_wall) || !(p->phi_min >= 0))
+    return fail(DDFLB_EINVAL, "non-finite boundary or reference value");
+  if (p->check_every < 0) return fail(DDFLB_EINVAL, "check_every < 0");
+  for (double s : {p->scale_f, p->scale_g}) {
+    if (s > 0) {
+      int e;
+      if (std::frexp(s, &e) != 0.5) return fail(DDFLB_EINVAL, "scale %g is not a power of two", s);
+    }
+  }
+  return DDFLB_OK;
+}
+
+LbParams make_lb(const ddflb_params* p, int pitch) {
+  LbParams P{};
+  P.nx = p->nx;
+  P.ny = p->ny;
+  P.pitch = pitch;
+  P.plane = (int64_t)pitch * p->ny;
+  for (int k = 0; k < 9; ++k) {
+    P.wf[k] = (float)p->omega_f[k];
+    P.wg[k] = (float)p->omega_g[k];
+  }
+  P.b1 = (float)p->beta1;
+  P.b2 = (float)p->beta2;
+  P.inv_db = (float)(1.0 / (p->beta1 - p->beta2));
+  P.cs2 = (float)p->cs2;
+  P.cs2p = (float)p->cs2_phi;
+  P.rho0 = (float)p->rho0;
+  P.phi0 = (float)p->phi0;
+  P.phimin = (float)p->phi_min;
+  const bool half = p->storage != DDFLB_FP32;
+  const double sf = half && p->scale_f > 0 ? p->scale_f : 1.0;
+  const double sg = half && p->scale_g > 0 ? p->scale_g : 1.0;
+  P.sf = (float)sf;
+  P.isf = (float)(1.0 / sf);
+  P.sg = (float)sg;
+  P.isg = (float)(1.0 / sg);
+  // rest weights from the equilibrium at u = 0 through the inverse of App. B:
+  // w0 = (1 - c)^2, w1..4 = c (1 - c) / 2, w5..8 = c^2 / 4
+  auto weights = [](double c, float* w) {
+    w[0] = (float)((1 - c) * (1 - c));
+    for (int a = 1; a <= 4; ++a) w[a] = (float)(c * (1 - c) / 2);
+    for (int a = 5; a <= 8; ++a) w[a] = (float)(c * c / 4);
+  };
+  weights(p->cs2, P.wrf);
+  weights(p->cs2_phi, P.wrg);
+  static const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+  for (int a = 0; a < 9; ++a) {
+    const double wf = P.wrf[a], wg = P.wrg[a];
+    P.lid[a] = (float)(2.0 * wf * p->rho0 * ex[a] * p->u_lid / p->cs2);
+    P.abb_lid[a] = (float)(2.0 * wg * (p->phi_lid - p->phi0));
+    P.abb_wall[a] = (float)(2.0 * wg * (p->phi_wall - p->phi0));
+  }
+  return P;
+}
+
+}  // namespace
+
+struct ddflb_ctx {
+  ddflb_params p;
+  Layout lay;
+  Launch L;
+  char* ws;
+  void* pops[2];
+  int cur;  // pops[cur] holds the current (post-collision, pre-stream) state
+  float* uprev;
+  double* partials;
+  DevStatus* status;
+  float* stage;
+  int64_t step;
+  int64_t snap_step;  // step at which uprev was last written (-1: none)
+};
+
+namespace {
+
+const void* fptr(const ddflb_ctx* c, int buf) { return c->pops[buf]; }
+
+// Zero the device status block (no residual yet, not diverged) on the stream.
+ddflb_status reset_status(ddflb_ctx* c) {
+  cudaError_t e = cudaMemsetAsync(c->status, 0, sizeof(DevStatus), c->L.stream);
+  return e == cudaSuccess ? DDFLB_OK : cuda_fail(e, "status reset");
+}
+
+const void* gptr(const ddflb_ctx* c, int buf) {
+  return (const char*)c->pops[buf] + 9 * c->lay.pitch * (size_t)c->p.ny * elem_size(c->p.storage);
+}
+
+ddflb_status check_launch(cudaError_t e, const char* where) {
+  return e == cudaSuccess ? DDFLB_OK : cuda_fail(e, where);
+}
+
+ddflb_status reduce(ddflb_ctx* c, int mode) {
+  cudaError_t e = launch_reduce(c->L, fptr(c, c->cur), gptr(c, c->cur), c->uprev, mode,
+                                c->partials, c->status);
+  if (e != cudaSuccess) return cuda_fail(e, "reduce");
+  if (mode & 2) c->snap_step = c->step;
+  return DDFLB_OK;
+}
+
+// residual bookkeeping around step s (state time): a snapshot of u at
+// s = K*j - 1 and a check against it at s = K*j.
+ddflb_status checks_at(ddflb_ctx* c) {
+  const int K = c->p.check_every;
+  if (K <= 0) return DDFLB_OK;
+  const int64_t s = c->step;
+  int mode = 0;
+  if (s > 0 && s % K == 0 && c->snap_step == s - 1) mode |= 1;
+  if (s % K == K - 1) mode |= 2;
+  if (mode == 0) return DDFLB_OK;
+  return reduce(c, mode);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t ddflb_workspace_bytes(const ddflb_params* p) {
+  if (validate(p) != DDFLB_OK) return 0;
+  return layout(p).total;
+}
+
+ddflb_status ddflb_create(const ddflb_params* p, void* ws, size_t bytes, void* stream,
+                          ddflb_ctx** out) {
+  if (!out) return fail(DDFLB_EINVAL, "out is NULL");
+  *out = nullptr;
+  ddflb_status s = validate(p);
+  if (s != DDFLB_OK) return s;
+  if (!ws) return fail(DDFLB_EINVAL, "workspace is NULL");
+  if ((uintptr_t)ws % kAlign) return fail(DDFLB_EINVAL, "workspace not %zu-byte aligned", kAlign);
+  const Layout lay = layout(p);
+  if (bytes < lay.total)
+    return fail(DDFLB_ENOMEM, "workspace %zu bytes < %zu required", bytes, lay.total);
+  ddflb_ctx* c = new (std::nothrow) ddflb_ctx();
+  if (!c) return fail(DDFLB_ENOMEM, "host allocation of the handle failed");
+  c->p = *p;
+  c->lay = lay;
+  c->ws = (char*)ws;
+  c->pops[0] = c->ws + lay.off_a;
+  c->pops[1] = c->ws + lay.off_b;
+  c->cur = 0;
+  c->uprev = (float*)(c->ws + lay.off_uprev);
+  c->partials = (double*)(c->ws + lay.off_part);
+  c->status = (DevStatus*)(c->ws + lay.off_status);
+  c->stage = (p->flags & DDFLB_FLAG_HOST_IO) ? (float*)(c->ws + lay.off_stage) : nullptr;
+  c->L.P = make_lb(p, lay.pitch);
+  c->L.P_bc = p->bc;
+  c->L.storage = p->storage;
+  c->L.block = dim3(128, 1, 1);
+  c->L.stream = (cudaStream_t)stream;
+  c->step = 0;
+  c->snap_step = -1;
+  ddflb_status st = reset_status(c);
+  if (st != DDFLB_OK) {
+    delete c;
+    return st;
+  }
+  *out = c;
+  return DDFLB_OK;
+}
+
+ddflb_status ddflb_init(ddflb_ctx* c, const float* rho, const float* ux, const float* uy,
+                        const float* phi, const float* grads) {
+  if (!c || !rho || !ux || !uy || !phi) return fail(DDFLB_EINVAL, "NULL handle or field");
+  if (grads) {
+    const double* wf = c->p.omega_f;
+    const double* wg = c->p.omega_g;
+    if (wf[3] <= 0 || wf[4] <= 0 || wf[5] <= 0 || wg[1] <= 0 || wg[2] <= 0 || wg[5] <= 0)
+      return fail(DDFLB_EINVAL, "gradient initialisation needs w3, w4, w5, w1^phi, w2^phi, "
+                                "w5^phi > 0");
+  }
+  ddflb_status s = reset_status(c);
+  if (s != DDFLB_OK) return s;
+  c->cur = 0;
+  c->step = 0;
+  c->snap_step = -1;
+  InitPtrs in{rho, ux, uy, phi, grads};
+  void* f = c->pops[0];
+  void* g = (char*)f + 9 * c->lay.pitch * (size_t)c->p.ny * elem_size(c->p.storage);
+  s = check_launch(launch_init(c->L, in, f, g), "init");
+  if (s != DDFLB_OK) return s;
+  return checks_at(c);
+}
+
+ddflb_status ddflb_init_host(ddflb_ctx* c, const float* rho, const float* ux, const float* uy,
+                             const float* phi, const float* grads) {
+  if (!c || !rho || !ux || !uy || !phi) return fail(DDFLB_EINVAL, "NULL handle or field");
+  if (!c->stage) return fail(DDFLB_EINVAL, "context created without DDFLB_FLAG_HOST_IO");
+  const size_t n = (size_t)c->p.nx * c->p.ny;
+  const float* src[5] = {rho, ux, uy, phi, grads};
+  const size_t planes[5] = {1, 1, 1, 1, 6};
+  float* dst[5];
+  size_t o = 0;
+  for (int k = 0; k < 5; ++k) {
+    dst[k] = c->stage + o * n;
+    o += planes[k];
+    if (!src[k]) continue;
+    cudaError_t e = cudaMemcpyAsync(dst[k], src[k], planes[k] * n * sizeof(float),
+                                    cudaMemcpyHostToDevice, c->L.stream);
+    if (e != cudaSuccess) return cuda_fail(e, "init_host copy");
+  }
+  return ddflb_init(c, dst[0], dst[1], dst[2], dst[3], grads ? dst[4] : nullptr);
+}
+
+ddflb_status ddflb_step(ddflb_ctx* c, int64_t n) {
+  if (!c) return fail(DDFLB_EINVAL, "NULL handle");
+  if (n < 0) return fail(DDFLB_EINVAL, "n < 0");
+  for (int64_t i = 0; i < n; ++i) {
+    const int src = c->cur, dst = c->cur ^ 1;
+    void* fo = c->pops[dst];
+    void* go = (char*)fo + 9 * c->lay.pitch * (size_t)c->p.ny * elem_size(c->p.storage);
+    cudaError_t e = launch_step(c->L, fptr(c, src), gptr(c, src), fo, go, c->status);
+    if (e != cudaSuccess) return cuda_fail(e, "step");
+    c->cur = dst;
+    ++c->step;
+    ddflb_status s = checks_at(c);
+    if (s != DDFLB_OK) return s;
+  }
+  return DDFLB_OK;
+}
+
+ddflb_status ddflb_fields(ddflb_ctx* c, float* rho, float* ux, float* uy, float* phi, float* sxx,
+                          float* sxy, float* syy, float* omega) {
+  if (!c) return fail(DDFLB_EINVAL, "NULL handle");
+  FieldPtrs fp{{rho, ux, uy, phi, sxx, sxy, syy, omega}};
+  return check_launch(launch_fields(c->L, fptr(c, c->cur), gptr(c, c->cur), fp), "fields");
+}
+
+ddflb_status ddflb_fields_host(ddflb_ctx* c, float* rho, float* ux, float* uy, float* phi,
+                               float* sxx, float* sxy, float* syy, float* omega) {
+  if (!c) return fail(DDFLB_EINVAL, "NULL handle");
+  if (!c->stage) return fail(DDFLB_EINVAL, "context created without DDFLB_FLAG_HOST_IO");
+  const size_t n = (size_t)c->p.nx * c->p.ny;
+  float* host[8] = {rho, ux, uy, phi, sxx, sxy, syy, omega};
+  FieldPtrs fp{};
+  for (int k = 0; k < 8; ++k) fp.p[k] = host[k] ? c->stage + k * n : nullptr;
+  ddflb_status s =
+      check_launch(launch_fields(c->L, fptr(c, c->cur), gptr(c, c->cur), fp), "fields_host");
+  if (s != DDFLB_OK) return s;
+  for (int k = 0; k < 8; ++k) {
+    if (!host[k]) continue;
+    cudaError_t e = cudaMemcpyAsync(host[k], fp.p[k], n * sizeof(float), cudaMemcpyDeviceToHost,
+                                    c->L.stream);
+    if (e != cudaSuccess) return cuda_fail(e, "fields_host copy");
+  }
+  cudaError_t e = cudaStreamSynchronize(c->L.stream);
+  return e == cudaSuccess ? DDFLB_OK : cuda_fail(e, "fields_host sync");
+}
+
+ddflb_status ddflb_populations(ddflb_ctx* c, float* f, float* g) {
+  if (!c) return fail(DDFLB_EINVAL, "NULL handle");
+  return check_launch(launch_pops(c->L, fptr(c, c->cur), gptr(c, c->cur), f, g), "populations");
+}
+
+ddflb_status ddflb_stats(ddflb_ctx* c, double* mass, double* scalar, double* residual,
+                         int64_t* step) {
+  if (!c) return fail(DDFLB_EINVAL, "NULL handle");
+  ddflb_status s = reduce(c, 0);
+  if (s != DDFLB_OK) return s;
+  DevStatus h{};
+  cudaError_t e = cudaMemcpyAsync(&h, c->status, sizeof h, cudaMemcpyDeviceToHost, c->L.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->L.stream);
+  if (e != cudaSuccess) return cuda_fail(e, "stats");
+  const double cells = (double)c->p.nx * c->p.ny;
+  if (mass) *mass = cells * c->p.rho0 + h.mass_dev;
+  if (scalar) *scalar = cells * c->p.phi0 + h.scalar_dev;
+  if (residual) *residual = h.has_residual ? h.residual : NAN;
+  if (step) *step = c->step;
+  if (h.diverged) return fail(DDFLB_EDIVERGED, "non-finite mass/scalar sum by step %lld",
+                              (long long)c->step);
+  return DDFLB_OK;
+}
+
+size_t ddflb_state_bytes(const ddflb_ctx* c) { return c ? c->lay.pops_bytes : 0; }
+
+ddflb_status ddflb_get_state(ddflb_ctx* c, void* dst, size_t bytes, int64_t* step) {
+  if (!c || !dst) return fail(DDFLB_EINVAL, "NULL argument");
+  if (bytes < c->lay.pops_bytes) return fail(DDFLB_ENOMEM, "state buffer too small");
+  cudaError_t e = cudaMemcpyAsync(dst, c->pops[c->cur], c->lay.pops_bytes,
+                                  cudaMemcpyDeviceToDevice, c->L.stream);
+  if (e != cudaSuccess) return cuda_fail(e, "get_state");
+  if (step) *step = c->step;
+  return DDFLB_OK;
+}
+
+ddflb_status ddflb_set_state(ddflb_ctx* c, const void* src, size_t bytes, int64_t step) {
+  if (!c || !src) return fail(DDFLB_EINVAL, "NULL argument");
+  if (bytes < c->lay.pops_bytes) return fail(DDFLB_ENOMEM, "state buffer too small");
+  if (step < 0) return fail(DDFLB_EINVAL, "step < 0");
+  cudaError_t e = cudaMemcpyAsync(c->pops[0], src, c->lay.pops_bytes, cudaMemcpyDeviceToDevice,
+                                  c->L.stream);
+  if (e != cudaSuccess) return cuda_fail(e, "set_state");
+  c->cur = 0;
+  c->step = step;
+  c->snap_step = -1;
+  return reset_status(c);
+}
+
+ddflb_status ddflb_destroy(ddflb_ctx* c) {
+  delete c;
+  return DDFLB_OK;
+}
+
+const char* ddflb_last_error(void) { return g_err.c_str(); }
+
+const char* ddflb_version(void) { return "ddflb 0.1 (sm_103a)"; }
+
+}  // extern "C"

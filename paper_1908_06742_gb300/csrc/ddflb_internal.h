@@ -1,0 +1,38 @@
+// Internal interface between the C ABI (ddflb_api.cu) and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ddflb_device.cuh"
+
+namespace ddflb {
+
+constexpr int kReduceThreads = 256;
+constexpr int kReduceBlocks = 608;  // 4 per SM on a 152-SM GB300; fixed for deterministic sums
+
+struct FieldPtrs {
+  float* p[8];  // rho, ux, uy, phi, sxx, sxy, syy, omega (any may be null)
+};
+
+struct InitPtrs {
+  const float *rho, *ux, *uy, *phi, *grads;
+};
+
+struct Launch {
+  LbParams P;
+  int P_bc;
+  int storage;  // 0 fp32, 1 fp16, 2 bf16
+  dim3 block;
+  cudaStream_t stream;
+};
+
+cudaError_t launch_step(const Launch& L, const void* fin, const void* gin, void* fout, void* gout,
+                        const DevStatus* st);
+cudaError_t launch_fields(const Launch& L, const void* fin, const void* gin, const FieldPtrs& out);
+cudaError_t launch_pops(const Launch& L, const void* fin, const void* gin, float* f, float* g);
+cudaError_t launch_init(const Launch& L, const InitPtrs& in, void* fout, void* gout);
+cudaError_t launch_reduce(const Launch& L, const void* fin, const void* gin, float* uprev,
+                          int mode, double* partials, DevStatus* st);
+
+}  // namespace ddflb

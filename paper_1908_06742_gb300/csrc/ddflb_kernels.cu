@@ -1,0 +1,340 @@
+// Kernels of the fused DDF lattice Boltzmann step for sm_103a, and their
+// launchers (host side, internal to the library).
+//
+//   k_step      one time step: pull both lattices with the wall rules, moments,
+//               MRT collision of both, back-transform, store (Secs. 2, 3, 5)
+//   k_fields    local kinematics of the current state (Sec. 4)
+//   k_pops      current pre-collision populations as full values
+//   k_init      equilibrium + Chapman-Enskog non-equilibrium initial state,
+//               written in the pre-streamed layout the pull step expects
+//   k_reduce    FP64 sums (mass, scalar, |u|^2, |u - u_prev|^2) per block
+//   k_finalize  fixed-order sum of the block partials into the status block
+//
+// The step is a memory-bound stencil: 18 populations read and 18 written per
+// node (144 B at FP32 storage), about 300 FP32 operations; no tensor cores.
+#include <cuda_runtime.h>
+
+#include "ddflb_device.cuh"
+#include "ddflb_internal.h"
+
+namespace ddflb {
+
+// ------------------------------------------------------------------ step
+template <typename S, int BC>
+__global__ void __launch_bounds__(256) k_step(LbParams P, const S* __restrict__ fin,
+                                              const S* __restrict__ gin, S* __restrict__ fout,
+                                              S* __restrict__ gout,
+                                              const DevStatus* __restrict__ status) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= P.nx || y >= P.ny) return;
+  if (status != nullptr && status->diverged) return;
+  float df[9], dg[9];
+  pull<S, BC>(P, fin, gin, x, y, df, dg);
+  Mom mf = moments(df), mg = moments(dg);
+  const Macro q = macro(P, mf, mg);
+  const Eq ef = eq_flow(P, mf.k0, q.rho, mf.kx, mf.ky, q.ux, q.uy);
+  const Eq eg = eq_scalar(P, mg.k0, q.phi, q.ux, q.uy);
+  relax_flow(P, mf, ef);
+  relax_scalar(P, mg, eg);
+  populations(mf, df);
+  populations(mg, dg);
+  const int64_t o = (int64_t)y * P.pitch + x;
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    Codec<S>::store(fout + a * P.plane + o, df[a], P.sf);
+    Codec<S>::store(gout + a * P.plane + o, dg[a], P.sg);
+  }
+}
+
+// ------------------------------------------------------------------ fields
+template <typename S, int BC>
+__global__ void __launch_bounds__(256) k_fields(LbParams P, const S* __restrict__ fin,
+                                                const S* __restrict__ gin, FieldPtrs out) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= P.nx || y >= P.ny) return;
+  float df[9], dg[9];
+  pull<S, BC>(P, fin, gin, x, y, df, dg);
+  const Mom mf = moments(df), mg = moments(dg);
+  const Macro q = macro(P, mf, mg);
+  const Eq ef = eq_flow(P, mf.k0, q.rho, mf.kx, mf.ky, q.ux, q.uy);
+  const Eq eg = eq_scalar(P, mg.k0, q.phi, q.ux, q.uy);
+  const Kin k = kinematics(P, mf, mg, q, ef, eg);
+  const int64_t o = (int64_t)y * P.nx + x;
+  if (out.p[0]) out.p[0][o] = q.rho;
+  if (out.p[1]) out.p[1][o] = q.ux;
+  if (out.p[2]) out.p[2][o] = q.uy;
+  if (out.p[3]) out.p[3][o] = q.phi;
+  if (out.p[4]) out.p[4][o] = k.sxx;
+  if (out.p[5]) out.p[5][o] = k.sxy;
+  if (out.p[6]) out.p[6][o] = k.syy;
+  if (out.p[7]) out.p[7][o] = k.omega;
+}
+
+// ------------------------------------------------------------------ populations
+template <typename S, int BC>
+__global__ void __launch_bounds__(256) k_pops(LbParams P, const S* __restrict__ fin,
+                                              const S* __restrict__ gin, float* __restrict__ fo,
+                                              float* __restrict__ go) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= P.nx || y >= P.ny) return;
+  float df[9], dg[9];
+  pull<S, BC>(P, fin, gin, x, y, df, dg);
+  const int64_t o = (int64_t)y * P.nx + x, n = (int64_t)P.nx * P.ny;
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    if (fo) fo[a * n + o] = df[a] + P.wrf[a] * P.rho0;
+    if (go) go[a * n + o] = dg[a] + P.wrg[a] * P.phi0;
+  }
+}
+
+// ------------------------------------------------------------------ init
+// Node (x, y) builds its populations at t = 0 and scatters them to the slots
+// the first pull will read: direction a goes to the upstream node x - e_a if
+// that node exists (periodic wrap included), otherwise (a wall link) into the
+// node's own slot of the opposite direction, with the wall rule undone.
+template <typename S, int BC>
+__global__ void __launch_bounds__(256) k_init(LbParams P, InitPtrs in, S* __restrict__ fout,
+                                              S* __restrict__ gout) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= P.nx || y >= P.ny) return;
+  const int64_t c = (int64_t)y * P.nx + x, n = (int64_t)P.nx * P.ny;
+  const float rho = in.rho[c], ux = in.ux[c], uy = in.uy[c], phi = in.phi[c];
+  const float k0 = rho - P.rho0, n0 = phi - P.phi0;
+  const float jx = rho * ux, jy = rho * uy;
+  const Eq ef = eq_flow(P, k0, rho, jx, jy, ux, uy);
+  const Eq eg = eq_scalar(P, n0, phi, ux, uy);
+  Mom mf{k0, jx, jy, ef.e3, ef.e4, ef.e5, ef.e6, ef.e7, ef.e8};
+  Mom mg{n0, eg.e1, eg.e2, eg.e3, eg.e4, eg.e5, eg.e6, eg.e7, eg.e8};
+  if (in.grads) {
+    // Chapman-Enskog non-equilibrium parts: Eqs. (strainratexxpyy)-(strainratexy)
+    // for the flow; Eqs. (1stnoneqmmomentx_CDE), (1stnoneqmmomenty_CDE),
+    // (offdiagonal2ndnoneqmmoment_CDE) for the scalar.
+    const float dxux = in.grads[c], dyux = in.grads[n + c];
+    const float dxuy = in.grads[2 * n + c], dyuy = in.grads[3 * n + c];
+    const float dxph = in.grads[4 * n + c], dyph = in.grads[5 * n + c];
+    mf.m3 += -2.0f * P.cs2 * rho / P.wf[3] * (dxux + dyuy);
+    mf.m4 += -2.0f * P.cs2 * rho / P.wf[4] * (dxux - dyuy);
+    mf.kxy += -P.cs2 * rho / P.wf[5] * (dxuy + dyux);
+    mg.kx += -P.cs2p / P.wg[1] * dxph;
+    mg.ky += -P.cs2p / P.wg[2] * dyph;
+    mg.kxy += -P.cs2p / P.wg[5] *
+              (phi * (P.b1 * dxuy + P.b2 * dyux) + P.b1 * uy * dxph + P.b2 * ux * dyph);
+  }
+  float df[9], dg[9];
+  populations(mf, df);
+  populations(mg, dg);
+  constexpr int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+  constexpr int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+  constexpr int opp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    int zx = x - ex[a], zy = y - ey[a];
+    bool wall = false, lid = false;
+    if (BC == BC_CAVITY) wall = zx < 0 || zx >= P.nx;
+    if (BC == BC_PERIODIC) {
+      zy = (zy + P.ny) % P.ny;
+    } else {
+      lid = zy >= P.ny;
+      wall = wall || zy < 0 || lid;
+    }
+    if (BC != BC_CAVITY) zx = (zx + P.nx) % P.nx;
+    if (!wall) {
+      const int64_t o = a * P.plane + (int64_t)zy * P.pitch + zx;
+      Codec<S>::store(fout + o, df[a], P.sf);
+      Codec<S>::store(gout + o, dg[a], P.sg);
+    } else {
+      const int64_t o = opp[a] * P.plane + (int64_t)y * P.pitch + x;
+      const float vf = df[a] - (lid ? P.lid[a] : 0.0f);
+      const float vg = (lid ? P.abb_lid[a] : P.abb_wall[a]) - dg[a];
+      Codec<S>::store(fout + o, vf, P.sf);
+      Codec<S>::store(gout + o, vg, P.sg);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ reductions
+// mode bit 1: compute |u - u_prev|^2 against the snapshot; bit 2: write the
+// current u as the new snapshot.  Partials: 4 doubles per block.
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename S, int BC>
+__global__ void __launch_bounds__(kReduceThreads) k_reduce(LbParams P, const S* __restrict__ fin,
+                                                           const S* __restrict__ gin,
+                                                           float* __restrict__ uprev, int mode,
+                                                           double* __restrict__ partials) {
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  const int64_t n = (int64_t)P.nx * P.ny;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int y = (int)(c / P.nx), x = (int)(c - (int64_t)y * P.nx);
+    float df[9], dg[9];
+    pull<S, BC>(P, fin, gin, x, y, df, dg);
+    const Mom mf = moments(df), mg = moments(dg);
+    const Macro q = macro(P, mf, mg);
+    s[0] += (double)mf.k0;
+    s[1] += (double)mg.k0;
+    s[2] += (double)q.ux * q.ux + (double)q.uy * q.uy;
+    if (mode & 1) {
+      const double ex = (double)q.ux - uprev[c], ey = (double)q.uy - uprev[n + c];
+      s[3] += ex * ex + ey * ey;
+    }
+    if (mode & 2) {
+      uprev[c] = q.ux;
+      uprev[n + c] = q.uy;
+    }
+  }
+  __shared__ double sh[kReduceThreads / 32][4];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double v = warp_sum(s[k]);
+    if (lane == 0) sh[warp][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double t = 0.0;
+    for (int w = 0; w < kReduceThreads / 32; ++w) t += sh[w][threadIdx.x];
+    partials[4 * blockIdx.x + threadIdx.x] = t;
+  }
+}
+
+// One block: thread k sums partials k, k + 256, ... (fixed order), then a
+// fixed tree.  mode bit 1: this reduction is a residual check.
+__global__ void __launch_bounds__(256) k_finalize(const double* __restrict__ partials, int nparts,
+                                                  int mode, DevStatus* __restrict__ st) {
+  __shared__ double sh[4][256];
+  for (int k = 0; k < 4; ++k) {
+    double t = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += 256) t += partials[4 * i + k];
+    sh[k][threadIdx.x] = t;
+  }
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    st->mass_dev = sh[0][0];
+    st->scalar_dev = sh[1][0];
+    st->u2 = sh[2][0];
+    if (mode & 1) {
+      st->du2 = sh[3][0];
+      st->residual = sh[2][0] > 0.0 ? sqrt(sh[3][0] / sh[2][0]) : 0.0;
+      st->has_residual = 1;
+    }
+    if (!isfinite(sh[0][0]) || !isfinite(sh[1][0]) || !isfinite(sh[2][0])) st->diverged = 1;
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+namespace {
+dim3 grid2d(const LbParams& P, dim3 b) {
+  return dim3((P.nx + b.x - 1) / b.x, (P.ny + b.y - 1) / b.y);
+}
+
+template <typename S>
+cudaError_t step_bc(const Launch& L, const void* fin, const void* gin, void* fout, void* gout,
+                    const DevStatus* st) {
+  const dim3 b = L.block, g = grid2d(L.P, b);
+  switch (L.P_bc) {
+    case BC_PERIODIC:
+      k_step<S, BC_PERIODIC><<<g, b, 0, L.stream>>>(L.P, (const S*)fin, (const S*)gin, (S*)fout,
+                                                    (S*)gout, st);
+      break;
+    case BC_CAVITY:
+      k_step<S, BC_CAVITY><<<g, b, 0, L.stream>>>(L.P, (const S*)fin, (const S*)gin, (S*)fout,
+                                                  (S*)gout, st);
+      break;
+    default:
+      k_step<S, BC_CHANNEL><<<g, b, 0, L.stream>>>(L.P, (const S*)fin, (const S*)gin, (S*)fout,
+                                                   (S*)gout, st);
+  }
+  return cudaGetLastError();
+}
+
+template <typename S, int BC>
+cudaError_t other_bc(const Launch& L, int what, const void* fin, const void* gin, void* a,
+                     void* b, const FieldPtrs* fp, const InitPtrs* ip, int mode, double* partials,
+                     int nparts) {
+  const dim3 blk = L.block, g = grid2d(L.P, blk);
+  switch (what) {
+    case 0:
+      k_fields<S, BC><<<g, blk, 0, L.stream>>>(L.P, (const S*)fin, (const S*)gin, *fp);
+      break;
+    case 1:
+      k_pops<S, BC><<<g, blk, 0, L.stream>>>(L.P, (const S*)fin, (const S*)gin, (float*)a,
+                                             (float*)b);
+      break;
+    case 2:
+      k_init<S, BC><<<g, blk, 0, L.stream>>>(L.P, *ip, (S*)a, (S*)b);
+      break;
+    default:
+      k_reduce<S, BC><<<nparts, kReduceThreads, 0, L.stream>>>(L.P, (const S*)fin, (const S*)gin,
+                                                               (float*)a, mode, partials);
+  }
+  return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t other(const Launch& L, int what, const void* fin, const void* gin, void* a, void* b,
+                  const FieldPtrs* fp, const InitPtrs* ip, int mode, double* partials, int np) {
+  switch (L.P_bc) {
+    case BC_PERIODIC:
+      return other_bc<S, BC_PERIODIC>(L, what, fin, gin, a, b, fp, ip, mode, partials, np);
+    case BC_CAVITY:
+      return other_bc<S, BC_CAVITY>(L, what, fin, gin, a, b, fp, ip, mode, partials, np);
+    default:
+      return other_bc<S, BC_CHANNEL>(L, what, fin, gin, a, b, fp, ip, mode, partials, np);
+  }
+}
+
+cudaError_t dispatch(const Launch& L, int what, const void* fin, const void* gin, void* a, void* b,
+                     const FieldPtrs* fp, const InitPtrs* ip, int mode, double* partials, int np) {
+  switch (L.storage) {
+    case 0: return other<float>(L, what, fin, gin, a, b, fp, ip, mode, partials, np);
+    case 1: return other<__half>(L, what, fin, gin, a, b, fp, ip, mode, partials, np);
+    default: return other<__nv_bfloat16>(L, what, fin, gin, a, b, fp, ip, mode, partials, np);
+  }
+}
+}  // namespace
+
+cudaError_t launch_step(const Launch& L, const void* fin, const void* gin, void* fout, void* gout,
+                        const DevStatus* st) {
+  switch (L.storage) {
+    case 0: return step_bc<float>(L, fin, gin, fout, gout, st);
+    case 1: return step_bc<__half>(L, fin, gin, fout, gout, st);
+    default: return step_bc<__nv_bfloat16>(L, fin, gin, fout, gout, st);
+  }
+}
+
+cudaError_t launch_fields(const Launch& L, const void* fin, const void* gin, const FieldPtrs& out) {
+  return dispatch(L, 0, fin, gin, nullptr, nullptr, &out, nullptr, 0, nullptr, 0);
+}
+
+cudaError_t launch_pops(const Launch& L, const void* fin, const void* gin, float* f, float* g) {
+  return dispatch(L, 1, fin, gin, f, g, nullptr, nullptr, 0, nullptr, 0);
+}
+
+cudaError_t launch_init(const Launch& L, const InitPtrs& in, void* fout, void* gout) {
+  return dispatch(L, 2, nullptr, nullptr, fout, gout, nullptr, &in, 0, nullptr, 0);
+}
+
+cudaError_t launch_reduce(const Launch& L, const void* fin, const void* gin, float* uprev,
+                          int mode, double* partials, DevStatus* st) {
+  cudaError_t e = dispatch(L, 3, fin, gin, uprev, nullptr, nullptr, nullptr, mode, partials,
+                           kReduceBlocks);
+  if (e != cudaSuccess) return e;
+  k_finalize<<<1, 256, 0, L.stream>>>(partials, kReduceBlocks, mode, st);
+  return cudaGetLastError();
+}
+
+}  // namespace ddflb

@@ -1,0 +1,270 @@
+"""Python binding of the C ABI in include/ddflb.h (argument marshalling only).
+
+Every step of the method runs in the CUDA library libddflb.so; this module
+loads it with ctypes, allocates the caller-owned device memory with PyTorch and
+passes raw pointers and the current CUDA stream.  There is no CPU fallback:
+without the built library every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libddflb.so")
+
+OK, EINVAL, ENOMEM, ECUDA, EDIVERGED, ENOTCONVERGED, ETIMEOUT = range(7)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EDIVERGED", "ENOTCONVERGED", "ETIMEOUT"]
+BC = {"periodic": 0, "cavity": 1, "channel": 2}
+STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
+FLAG_HOST_IO = 1
+FIELD_NAMES = ("rho", "ux", "uy", "phi", "sxx", "sxy", "syy", "omega")
+
+
+class DdflbError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 7 else status}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    """Mirror of ddflb_params."""
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("bc", ctypes.c_int32), ("storage", ctypes.c_int32),
+        ("omega_f", ctypes.c_double * 9), ("omega_g", ctypes.c_double * 9),
+        ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+        ("cs2", ctypes.c_double), ("cs2_phi", ctypes.c_double),
+        ("rho0", ctypes.c_double), ("phi0", ctypes.c_double),
+        ("u_lid", ctypes.c_double), ("phi_lid", ctypes.c_double), ("phi_wall", ctypes.c_double),
+        ("phi_min", ctypes.c_double),
+        ("scale_f", ctypes.c_double), ("scale_g", ctypes.c_double),
+        ("check_every", ctypes.c_int32), ("flags", ctypes.c_int32),
+    ]
+
+
+_VP = ctypes.c_void_p
+_FP = ctypes.c_void_p  # device pointers travel as integers
+_lib = None
+
+# name -> (restype, argtypes); every symbol declared in include/ddflb.h
+SIGNATURES = {
+    "ddflb_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(Params)]),
+    "ddflb_create": (ctypes.c_int, [ctypes.POINTER(Params), _VP, ctypes.c_size_t, _VP,
+                                    ctypes.POINTER(_VP)]),
+    "ddflb_init": (ctypes.c_int, [_VP, _FP, _FP, _FP, _FP, _FP]),
+    "ddflb_init_host": (ctypes.c_int, [_VP, _FP, _FP, _FP, _FP, _FP]),
+    "ddflb_step": (ctypes.c_int, [_VP, ctypes.c_int64]),
+    "ddflb_fields": (ctypes.c_int, [_VP] + [_FP] * 8),
+    "ddflb_fields_host": (ctypes.c_int, [_VP] + [_FP] * 8),
+    "ddflb_populations": (ctypes.c_int, [_VP, _FP, _FP]),
+    "ddflb_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_int64)]),
+    "ddflb_state_bytes": (ctypes.c_size_t, [_VP]),
+    "ddflb_get_state": (ctypes.c_int, [_VP, _FP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int64)]),
+    "ddflb_set_state": (ctypes.c_int, [_VP, _FP, ctypes.c_size_t, ctypes.c_int64]),
+    "ddflb_destroy": (ctypes.c_int, [_VP]),
+    "ddflb_last_error": (ctypes.c_char_p, []),
+    "ddflb_version": (ctypes.c_char_p, []),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load libddflb.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} not built: run __graft_entry__.build() "
+                           "(there is no CPU fallback)")
+    L = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != OK:
+        raise DdflbError(status, load().ddflb_last_error().decode())
+
+
+def relaxation_rate(diffusivity: float, cs2: float = 1.0 / 3.0) -> float:
+    """omega for a viscosity or diffusivity: nu = cs2 (1/omega - 1/2) (Secs. 2, 3)."""
+    return 1.0 / (diffusivity / cs2 + 0.5)
+
+
+@dataclasses.dataclass
+class Config:
+    """User-facing parameters; ``to_c`` fills the ABI struct."""
+    nx: int
+    ny: int
+    bc: str = "periodic"
+    storage: str = "fp32"
+    nu: float = 0.01            # kinematic viscosity -> omega_4 = omega_5
+    diffusivity: float = 0.01   # D_phi -> omega_1^phi = omega_2^phi
+    omega_bulk: float = 1.2     # omega_3
+    omega_hi: float = 1.2       # omega_6..8
+    omega_phi_hi: float = 1.2   # omega_3^phi..omega_8^phi
+    beta1: float = 1.0
+    beta2: float = 0.9
+    cs2: float = 1.0 / 3.0
+    cs2_phi: float = 1.0 / 3.0
+    rho0: float = 1.0
+    phi0: float = 1.0
+    u_lid: float = 0.0
+    phi_lid: float = 1.0
+    phi_wall: float = 0.0
+    phi_min: float = 1e-3
+    scale_f: float = 0.0
+    scale_g: float = 0.0
+    check_every: int = 0
+    host_io: bool = False
+    omega_f: Optional[tuple] = None   # explicit 9-entry diagonals override the above
+    omega_g: Optional[tuple] = None
+
+    def rates(self):
+        wf = self.omega_f or (0.0, 0.0, 0.0, self.omega_bulk, relaxation_rate(self.nu, self.cs2),
+                              relaxation_rate(self.nu, self.cs2), self.omega_hi, self.omega_hi,
+                              self.omega_hi)
+        wphi = relaxation_rate(self.diffusivity, self.cs2_phi)
+        h = self.omega_phi_hi
+        wg = self.omega_g or (0.0, wphi, wphi, h, h, h, h, h, h)
+        return tuple(wf), tuple(wg)
+
+    def to_c(self) -> Params:
+        p = Params()
+        p.nx, p.ny = self.nx, self.ny
+        p.bc, p.storage = BC[self.bc], STORAGE[self.storage]
+        wf, wg = self.rates()
+        for k in range(9):
+            p.omega_f[k] = wf[k]
+            p.omega_g[k] = wg[k]
+        p.beta1, p.beta2 = self.beta1, self.beta2
+        p.cs2, p.cs2_phi = self.cs2, self.cs2_phi
+        p.rho0, p.phi0 = self.rho0, self.phi0
+        p.u_lid, p.phi_lid, p.phi_wall = self.u_lid, self.phi_lid, self.phi_wall
+        p.phi_min = self.phi_min
+        p.scale_f, p.scale_g = self.scale_f, self.scale_g
+        p.check_every = self.check_every
+        p.flags = FLAG_HOST_IO if self.host_io else 0
+        return p
+
+
+def workspace_bytes(cfg: Config) -> int:
+    p = cfg.to_c()
+    n = load().ddflb_workspace_bytes(ctypes.byref(p))
+    if n == 0:
+        _check(EINVAL)
+    return n
+
+
+def _dptr(t) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+class Lattice:
+    """One pair of D2Q9 lattices (flow f, scalar g) resident on the GPU."""
+
+    def __init__(self, cfg: Config, device=None, stream=None):
+        import torch
+        self.torch = torch
+        self.cfg = cfg
+        self.device = torch.device(device or "cuda")
+        self.lib = load()
+        self._p = cfg.to_c()
+        nbytes = workspace_bytes(cfg)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream or torch.cuda.current_stream(self.device)
+        h = _VP()
+        _check(self.lib.ddflb_create(ctypes.byref(self._p), self.workspace.data_ptr(), nbytes,
+                                     self.stream.cuda_stream, ctypes.byref(h)))
+        self._h = h
+        self.shape = (cfg.ny, cfg.nx)
+
+    # -- helpers
+    def _dev(self, a):
+        t = self.torch
+        if a is None:
+            return None
+        if isinstance(a, np.ndarray):
+            a = t.from_numpy(np.ascontiguousarray(a, dtype=np.float32))
+        return a.to(device=self.device, dtype=t.float32).contiguous()
+
+    def _empty(self, *lead):
+        return self.torch.empty(*lead, *self.shape, dtype=self.torch.float32, device=self.device)
+
+    # -- ABI
+    def init(self, rho, ux, uy, phi, grads=None):
+        self._keep = [self._dev(a) for a in (rho, ux, uy, phi, grads)]
+        r, u, v, p, g = self._keep
+        _check(self.lib.ddflb_init(self._h, _dptr(r), _dptr(u), _dptr(v), _dptr(p), _dptr(g)))
+        return self
+
+    def init_host(self, rho, ux, uy, phi, grads=None):
+        """Host (CPU, ideally pinned) float32 tensors; copies run inside the call."""
+        args = [None if a is None else a.data_ptr() for a in (rho, ux, uy, phi, grads)]
+        _check(self.lib.ddflb_init_host(self._h, *args))
+        return self
+
+    def step(self, n: int = 1):
+        _check(self.lib.ddflb_step(self._h, int(n)))
+        return self
+
+    def fields(self, names=FIELD_NAMES) -> dict:
+        out = {k: (self._empty() if k in names else None) for k in FIELD_NAMES}
+        _check(self.lib.ddflb_fields(self._h, *[_dptr(out[k]) for k in FIELD_NAMES]))
+        return {k: v for k, v in out.items() if v is not None}
+
+    def fields_host(self, out: dict) -> dict:
+        """Write fields into host float32 tensors given by name (synchronises)."""
+        _check(self.lib.ddflb_fields_host(
+            self._h, *[(out[k].data_ptr() if k in out else None) for k in FIELD_NAMES]))
+        return out
+
+    def populations(self):
+        f, g = self._empty(9), self._empty(9)
+        _check(self.lib.ddflb_populations(self._h, f.data_ptr(), g.data_ptr()))
+        return f, g
+
+    def stats(self) -> dict:
+        m, s, r = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        k = ctypes.c_int64()
+        st = self.lib.ddflb_stats(self._h, ctypes.byref(m), ctypes.byref(s), ctypes.byref(r),
+                                  ctypes.byref(k))
+        if st not in (OK, EDIVERGED):
+            _check(st)
+        return {"mass": m.value, "scalar": s.value, "residual": r.value, "step": k.value,
+                "diverged": st == EDIVERGED}
+
+    def state_bytes(self) -> int:
+        return self.lib.ddflb_state_bytes(self._h)
+
+    def get_state(self):
+        buf = self.torch.empty(self.state_bytes(), dtype=self.torch.uint8, device=self.device)
+        k = ctypes.c_int64()
+        _check(self.lib.ddflb_get_state(self._h, buf.data_ptr(), buf.numel(), ctypes.byref(k)))
+        return buf, k.value
+
+    def set_state(self, buf, step: int):
+        _check(self.lib.ddflb_set_state(self._h, buf.data_ptr(), buf.numel(), int(step)))
+        return self
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.ddflb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

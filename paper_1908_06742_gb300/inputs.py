@@ -25,27 +25,41 @@ class Fields:
 
 
 def taylor_green(n: int, u0: float = 0.01, phi_amp: float = 0.1, rho0: float = 1.0,
-                 cs2: float = 1.0 / 3.0, ny: int | None = None) -> Fields:
+                 cs2: float = 1.0 / 3.0, ny: int | None = None, window=None,
+                 xp=np, device=None) -> Fields:
     """Decaying Taylor-Green vortex at t = 0 on a periodic n x n grid.
 
     u_x = -u0 cos(kx) sin(ky), u_y = u0 sin(kx) cos(ky), k = 2 pi / n,
     pressure p = -rho0 u0^2 / 4 (cos 2kx + cos 2ky), rho = rho0 + p / c_s^2,
     scalar phi = 1 + phi_amp sin(kx) sin(ky).  Exact gradients are returned for
     the Chapman-Enskog initialisation of the populations.
+
+    ``window = (x0, y0, w, h)`` returns only that sub-rectangle of the grid
+    (indices taken modulo the period); ``xp = torch`` with ``device`` builds the
+    fields directly in device memory (float64), for grids too large for the host.
     """
     ny = n if ny is None else ny
     kx = 2.0 * math.pi / n
     ky = 2.0 * math.pi / ny
-    x = np.arange(n, dtype=np.float64)[None, :]
-    y = np.arange(ny, dtype=np.float64)[:, None]
-    cx, sx = np.cos(kx * x), np.sin(kx * x)
-    cy, sy = np.cos(ky * y), np.sin(ky * y)
+    x0, y0, w, h = window if window is not None else (0, 0, n, ny)
+    if xp is np:
+        xs = (np.arange(w, dtype=np.int64) + x0) % n
+        ys = (np.arange(h, dtype=np.int64) + y0) % ny
+        x = xs.astype(np.float64)[None, :]
+        y = ys.astype(np.float64)[:, None]
+    else:
+        xs = (xp.arange(w, dtype=xp.int64, device=device) + x0) % n
+        ys = (xp.arange(h, dtype=xp.int64, device=device) + y0) % ny
+        x = xs.to(xp.float64)[None, :]
+        y = ys.to(xp.float64)[:, None]
+    cx, sx = xp.cos(kx * x), xp.sin(kx * x)
+    cy, sy = xp.cos(ky * y), xp.sin(ky * y)
     ux = -u0 * cx * sy
     uy = u0 * sx * cy
-    p = -rho0 * u0 * u0 / 4.0 * (np.cos(2 * kx * x) + np.cos(2 * ky * y))
+    p = -rho0 * u0 * u0 / 4.0 * (xp.cos(2 * kx * x) + xp.cos(2 * ky * y))
     rho = rho0 + p / cs2
     phi = 1.0 + phi_amp * sx * sy
-    grads = np.stack([
+    grads = xp.stack([
         u0 * kx * sx * sy,             # d_x u_x
         -u0 * ky * cx * cy,            # d_y u_x
         u0 * kx * cx * cy,             # d_x u_y
@@ -53,8 +67,11 @@ def taylor_green(n: int, u0: float = 0.01, phi_amp: float = 0.1, rho0: float = 1
         phi_amp * kx * cx * sy,        # d_x phi
         phi_amp * ky * sx * cy,        # d_y phi
     ])
-    b = lambda a: np.ascontiguousarray(np.broadcast_to(a, (ny, n)), np.float64)
-    return Fields(b(rho), b(ux), b(uy), b(phi), np.ascontiguousarray(grads, np.float64))
+    if xp is np:
+        b = lambda a: np.ascontiguousarray(np.broadcast_to(a, (h, w)), np.float64)
+        return Fields(b(rho), b(ux), b(uy), b(phi), np.ascontiguousarray(grads, np.float64))
+    b = lambda a: xp.broadcast_to(a, (h, w)).contiguous()
+    return Fields(b(rho), b(ux), b(uy), b(phi), grads.contiguous())
 
 
 def rest(nx: int, ny: int, rho0: float = 1.0, phi: float = 0.0) -> Fields:
