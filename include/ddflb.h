@@ -81,7 +81,7 @@ typedef struct {
   double omega_f[9];
   double omega_g[9];
   double beta1, beta2;  /* scalar-flux anisotropy, |beta1 - beta2| > 1e-6 (Sec. 4) */
-  double cs2, cs2_phi;  /* c_s^2 and c_sphi^2 (1/3 in the paper)                   */
+  double cs2, cs2_phi;  /* c_s^2 and c_sphi^2: must be 1/3 (as in all of Sec. 5)    */
   double rho0, phi0;    /* rest state: storage offsets; rho0 also in the lid term   */
   double u_lid;         /* x velocity of the moving wall (cavity, channel)          */
   double phi_lid;       /* scalar value held by the moving wall                     */

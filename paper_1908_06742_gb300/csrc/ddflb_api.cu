@@ -86,8 +86,8 @@ ddflb_status validate(const ddflb_params* p) {
   if (!(std::fabs(p->beta1 - p->beta2) > 1e-6))
     return fail(DDFLB_EINVAL, "beta1 - beta2 = %g: the vorticity needs beta1 != beta2",
                 p->beta1 - p->beta2);
-  if (!(p->cs2 > 0 && p->cs2 < 1) || !(p->cs2_phi > 0 && p->cs2_phi < 1))
-    return fail(DDFLB_EINVAL, "cs2, cs2_phi must lie in (0, 1)");
+  if (std::fabs(p->cs2 - 1.0 / 3.0) > 1e-12 || std::fabs(p->cs2_phi - 1.0 / 3.0) > 1e-12)
+    return fail(DDFLB_EINVAL, "cs2 and cs2_phi must be 1/3 (the D2Q9 rest weights)");
   if (!std::isfinite(p->rho0) || p->rho0 <= 0) return fail(DDFLB_EINVAL, "rho0 must be > 0");
   if (!std::isfinite(p->phi0) || !std::isfinite(p->u_lid) || !std::isfinite(p->phi_lid) ||
       !std::isfinite(p->phi_wall) || !(p->phi_min >= 0))

@@ -142,150 +142,183 @@ __device__ __forceinline__ void pull(const LbParams& P, const S* __restrict__ fi
 }
 
 // ------------------------------------------------------------ moments
-// Raw moments of the deviations in the order of Eq. (basisvectors):
-// (k0, kx, ky, kxx + kyy, kxx - kyy, kxy, kxxy, kxyy, kxxyy).
+// Raw moments of the deviations in the basis of Eq. (basisvectors), with the
+// two even moments that carry the rest state taken relative to it:
+//   m3h = (kxx + kyy) - 2 c k0,  m8h = kxxyy - c^2 k0   (c = c_s^2 = 1/3),
+// which are exactly the parts the rest-state equilibrium does not cancel.
+//
+// Summation order is chosen per lattice so that the dominant parts cancel
+// exactly before any rounding (Sterbenz: a - b is exact for b/2 <= a <= 2b):
+//  - the flow deviations are dominated by the O(u) odd part, so opposite
+//    directions are added first (f_a + f_abar is small and exact);
+//  - the scalar deviations are dominated by w_a (phi - phi0), so equal-weight
+//    directions are differenced first, and the rest-part combinations
+//    sum_a d_a (|e_a|^2 - 2c) and sum_a d_a (e_ax^2 e_ay^2 - c^2) are formed
+//    from differences against q = d_0 / 4 (w_0 / 4 = w_1 = 4 w_5 at c = 1/3).
 struct Mom {
-  float k0, kx, ky, m3, m4, kxy, kxxy, kxyy, kxxyy;
+  float k0, kx, ky, m3h, m4, kxy, kxxy, kxyy, m8h;
 };
 
-__device__ __forceinline__ Mom moments(const float d[9]) {
+__device__ __forceinline__ Mom moments_flow(const float d[9]) {
   Mom m;
-  const float s5 = d[5] + d[7], s6 = d[6] + d[8];
-  const float a5 = d[5] - d[7], a6 = d[6] - d[8];
-  m.kxxyy = s5 + s6;
-  m.kxy = s5 - s6;
-  m.kxxy = a5 + a6;
-  m.kxyy = a5 - a6;
-  const float dx = d[1] - d[3], dy = d[2] - d[4];
-  m.kx = dx + m.kxyy;
-  m.ky = dy + m.kxxy;
-  const float kxx = d[1] + d[3] + m.kxxyy;
-  const float kyy = d[2] + d[4] + m.kxxyy;
-  m.m3 = kxx + kyy;
-  m.m4 = kxx - kyy;
-  m.k0 = d[0] + (d[1] + d[2]) + (d[3] + d[4]) + m.kxxyy;
+  const float s57 = d[5] + d[7], s68 = d[6] + d[8];
+  const float a57 = d[5] - d[7], a68 = d[6] - d[8];
+  m.kxy = s57 - s68;
+  m.kxxy = a57 + a68;
+  m.kxyy = a57 - a68;
+  m.kx = (d[1] - d[3]) + m.kxyy;
+  m.ky = (d[2] - d[4]) + m.kxxy;
+  const float s13 = d[1] + d[3], s24 = d[2] + d[4];
+  m.m4 = s13 - s24;
+  const float A = s13 + s24, B = s57 + s68;
+  m.m3h = ((A + 4.0f * B) - 2.0f * d[0]) * (1.0f / 3.0f);
+  m.m8h = ((8.0f * B - A) - d[0]) * (1.0f / 9.0f);
+  m.k0 = d[0] + (A + B);
   return m;
 }
 
-// Back to populations with the explicit inverse of App. B (kxx, kyy from
-// m3 = kxx + kyy and m4 = kxx - kyy).
-__device__ __forceinline__ void populations(const Mom& m, float d[9]) {
-  const float kxx = 0.5f * (m.m3 + m.m4), kyy = 0.5f * (m.m3 - m.m4);
-  d[0] = m.k0 - m.m3 + m.kxxyy;
-  d[1] = 0.5f * (m.kx + kxx - m.kxyy - m.kxxyy);
-  d[2] = 0.5f * (m.ky + kyy - m.kxxy - m.kxxyy);
-  d[3] = 0.5f * (-m.kx + kxx + m.kxyy - m.kxxyy);
-  d[4] = 0.5f * (-m.ky + kyy + m.kxxy - m.kxxyy);
-  const float p = m.kxy + m.kxxyy, q = m.kxxy + m.kxyy;
-  const float r = m.kxxyy - m.kxy, s = m.kxxy - m.kxyy;
+__device__ __forceinline__ Mom moments_scalar(const float d[9]) {
+  Mom m;
+  const float a57 = d[5] - d[7], a68 = d[6] - d[8];
+  m.kxy = (d[5] - d[6]) + (d[7] - d[8]);
+  m.kxxy = a57 + a68;
+  m.kxyy = a57 - a68;
+  m.kx = (d[1] - d[3]) + m.kxyy;
+  m.ky = (d[2] - d[4]) + m.kxxy;
+  m.m4 = (d[1] - d[2]) + (d[3] - d[4]);
+  const float q = 0.25f * d[0];
+  const float t1 = ((d[1] - q) + (d[3] - q)) + ((d[2] - q) + (d[4] - q));
+  const float t2 = ((4.0f * d[5] - q) + (4.0f * d[7] - q)) + ((4.0f * d[6] - q) + (4.0f * d[8] - q));
+  m.m3h = (t1 + t2) * (1.0f / 3.0f);
+  const float u5 = (8.0f * d[5] - q) - d[1], u6 = (8.0f * d[6] - q) - d[2];
+  const float u7 = (8.0f * d[7] - q) - d[3], u8 = (8.0f * d[8] - q) - d[4];
+  m.m8h = ((u5 + u7) + (u6 + u8)) * (1.0f / 9.0f);
+  m.k0 = d[0] + ((d[1] + d[3]) + (d[2] + d[4])) + ((d[5] + d[7]) + (d[6] + d[8]));
+  return m;
+}
+
+// Populations from raw moments (deviation form, m3 = kxx + kyy and
+// m8 = kxxyy in full) with the explicit inverse of App. B.
+__device__ __forceinline__ void populations(float k0, float kx, float ky, float m3, float m4,
+                                            float kxy, float kxxy, float kxyy, float kxxyy,
+                                            float d[9]) {
+  const float kxx = 0.5f * (m3 + m4), kyy = 0.5f * (m3 - m4);
+  d[0] = k0 - m3 + kxxyy;
+  d[1] = 0.5f * (kx + kxx - kxyy - kxxyy);
+  d[2] = 0.5f * (ky + kyy - kxxy - kxxyy);
+  d[3] = 0.5f * (-kx + kxx + kxyy - kxxyy);
+  d[4] = 0.5f * (-ky + kyy + kxxy - kxxyy);
+  const float p = kxy + kxxyy, q = kxxy + kxyy;
+  const float r = kxxyy - kxy, s = kxxy - kxyy;
   d[5] = 0.25f * (p + q);
   d[6] = 0.25f * (r + s);
   d[7] = 0.25f * (p - q);
   d[8] = 0.25f * (r - s);
 }
 
-// Equilibrium moments in deviation form (moment minus its rest value).
-// Flow: Eq. (eqmrawmoment); scalar: Eq. (eqmrawmoment_CDE) with beta1, beta2.
-struct Eq {
-  float e1, e2, e3, e4, e5, e6, e7, e8;
-};
-
-__device__ __forceinline__ Eq eq_flow(const LbParams& P, float k0, float rho, float jx, float jy,
-                                      float ux, float uy) {
-  Eq e;
-  const float c = P.cs2, uxx = ux * ux, uyy = uy * uy, usq = uxx + uyy;
-  e.e1 = jx;
-  e.e2 = jy;
-  e.e3 = 2.0f * c * k0 + rho * usq;
-  e.e4 = rho * (uxx - uyy);
-  e.e5 = jx * uy;
-  e.e6 = jy * (c + uxx);
-  e.e7 = jx * (c + uyy);
-  e.e8 = c * c * k0 + rho * (c * usq + uxx * uyy);
-  return e;
-}
-
-__device__ __forceinline__ Eq eq_scalar(const LbParams& P, float n0, float phi, float ux, float uy) {
-  Eq e;
-  const float c = P.cs2p, uxx = ux * ux, uyy = uy * uy, usq = uxx + uyy;
-  const float px = phi * ux, py = phi * uy;
-  e.e1 = px;
-  e.e2 = py;
-  e.e3 = 2.0f * c * n0 + phi * usq;
-  e.e4 = phi * (uxx - uyy);
-  e.e5 = px * uy;
-  e.e6 = py * (P.b1 * c + uxx);
-  e.e7 = px * (P.b2 * c + uyy);
-  e.e8 = c * c * n0 + phi * (c * usq + uxx * uyy);
-  return e;
-}
-
 // Macroscopic state of a node (Eq. hydrodynamic_fields with F = 0; phi = sum g).
 struct Macro {
-  float rho, ux, uy, phi;
+  float rho, irho, ux, uy, phi;
 };
 
 __device__ __forceinline__ Macro macro(const LbParams& P, const Mom& mf, const Mom& mg) {
   Macro q;
   q.rho = P.rho0 + mf.k0;
-  const float inv = __frcp_rn(q.rho);
-  q.ux = mf.kx * inv;
-  q.uy = mf.ky * inv;
+  q.irho = __frcp_rn(q.rho);
+  q.ux = mf.kx * q.irho;
+  q.uy = mf.ky * q.irho;
   q.phi = P.phi0 + mg.k0;
   return q;
 }
 
-// MRT relaxation in moment space, m* = m - Lambda (m - m^eq).
-__device__ __forceinline__ void relax_flow(const LbParams& P, Mom& m, const Eq& e) {
-  m.m3 -= P.wf[3] * (m.m3 - e.e3);
-  m.m4 -= P.wf[4] * (m.m4 - e.e4);
-  m.kxy -= P.wf[5] * (m.kxy - e.e5);
-  m.kxxy -= P.wf[6] * (m.kxxy - e.e6);
-  m.kxyy -= P.wf[7] * (m.kxyy - e.e7);
-  m.kxxyy -= P.wf[8] * (m.kxxyy - e.e8);
+// Non-equilibrium moments m - m^eq (entries 1..8 of Eq. (basisvectors)); the
+// equilibria are Eq. (eqmrawmoment) for the flow and Eq. (eqmrawmoment_CDE)
+// for the scalar, written relative to the rest state like Mom (c = 1/3):
+//   m3^eq - 2c k0 = rho |u|^2,  m8^eq - c^2 k0 = rho (c |u|^2 + ux^2 uy^2).
+struct Neq {
+  float n1, n2, n3, n4, n5, n6, n7, n8;
+};
+
+__device__ __forceinline__ Neq neq_flow(const Mom& m, const Macro& q) {
+  Neq n;
+  const float c = 1.0f / 3.0f;
+  const float uxx = q.ux * q.ux, uyy = q.uy * q.uy, usq = uxx + uyy;
+  n.n1 = 0.0f;  // momentum is conserved
+  n.n2 = 0.0f;
+  n.n3 = m.m3h - q.rho * usq;
+  n.n4 = m.m4 - q.rho * (uxx - uyy);
+  n.n5 = m.kxy - m.kx * q.uy;
+  n.n6 = m.kxxy - m.ky * (c + uxx);
+  n.n7 = m.kxyy - m.kx * (c + uyy);
+  n.n8 = m.m8h - q.rho * (c * usq + uxx * uyy);
+  return n;
 }
 
-__device__ __forceinline__ void relax_scalar(const LbParams& P, Mom& n, const Eq& e) {
-  n.kx -= P.wg[1] * (n.kx - e.e1);
-  n.ky -= P.wg[2] * (n.ky - e.e2);
-  n.m3 -= P.wg[3] * (n.m3 - e.e3);
-  n.m4 -= P.wg[4] * (n.m4 - e.e4);
-  n.kxy -= P.wg[5] * (n.kxy - e.e5);
-  n.kxxy -= P.wg[6] * (n.kxxy - e.e6);
-  n.kxyy -= P.wg[7] * (n.kxyy - e.e7);
-  n.kxxyy -= P.wg[8] * (n.kxxyy - e.e8);
+__device__ __forceinline__ Neq neq_scalar(const LbParams& P, const Mom& g, const Mom& f,
+                                          const Macro& q) {
+  Neq n;
+  const float c = 1.0f / 3.0f;
+  const float uxx = q.ux * q.ux, uyy = q.uy * q.uy, usq = uxx + uyy;
+  const float px = q.phi * q.ux, py = q.phi * q.uy;
+  // first order: eta_x - phi u_x = (eta_x rho - phi j_x) / rho, with the product
+  // phi j_x split exactly by an FMA so only the small result is rounded
+  const float tx = q.phi * f.kx, ex = __fmaf_rn(q.phi, f.kx, -tx);
+  const float ty = q.phi * f.ky, ey = __fmaf_rn(q.phi, f.ky, -ty);
+  n.n1 = (__fmaf_rn(g.kx, q.rho, -tx) - ex) * q.irho;
+  n.n2 = (__fmaf_rn(g.ky, q.rho, -ty) - ey) * q.irho;
+  n.n3 = g.m3h - q.phi * usq;
+  n.n4 = g.m4 - q.phi * (uxx - uyy);
+  n.n5 = g.kxy - px * q.uy;
+  n.n6 = g.kxxy - py * (P.b1 * c + uxx);
+  n.n7 = g.kxyy - px * (P.b2 * c + uyy);
+  n.n8 = g.m8h - q.phi * (c * usq + uxx * uyy);
+  return n;
+}
+
+// Collision in increment form: f*_a = f_a - [T^-1 Lambda (m - m^eq)]_a
+// (Eqs. MRT-LBEfluidmotion_transformed with F = 0, MRT-LBECDE), so that only
+// the small increment is built from moments and the stored value is rounded
+// once.  w[] holds the relaxation rates of the lattice (w[0] = 0).
+__device__ __forceinline__ void relax(const float w[9], const Neq& n, float d[9]) {
+  const float d1 = w[1] * n.n1, d2 = w[2] * n.n2, d3 = w[3] * n.n3, d4 = w[4] * n.n4;
+  const float d5 = w[5] * n.n5, d6 = w[6] * n.n6, d7 = w[7] * n.n7, d8 = w[8] * n.n8;
+  const float dxx = 0.5f * (d3 + d4), dyy = 0.5f * (d3 - d4);
+  d[0] -= d8 - d3;
+  d[1] -= 0.5f * (d1 + dxx - d7 - d8);
+  d[2] -= 0.5f * (d2 + dyy - d6 - d8);
+  d[3] -= 0.5f * (-d1 + dxx + d7 - d8);
+  d[4] -= 0.5f * (-d2 + dyy + d6 - d8);
+  const float p = d5 + d8, q = d6 + d7, r = d8 - d5, s = d6 - d7;
+  d[5] -= 0.25f * (p + q);
+  d[6] -= 0.25f * (r + s);
+  d[7] -= 0.25f * (p - q);
+  d[8] -= 0.25f * (r - s);
 }
 
 // ------------------------------------------------------------ local kinematics
-// Sec. 4: from the pre-collision non-equilibrium moments
-//   m3' = m3 - m3^eq, m4' = m4 - m4^eq, m5' = kxy - rho ux uy       (flow)
-//   n1' = eta_x - phi ux, n2' = eta_y - phi uy, n5' = eta_xy - phi ux uy (scalar)
-// d_i phi = -(w_i^phi / cs2p) n_i';  N = -w5 m5' / (rho cs2);
-// N^phi = -w5^phi n5' / (phi cs2p) - (b1 uy dxphi + b2 ux dyphi) / phi;
-// dxuy = (N^phi - b2 N)/(b1 - b2), dyux = (b1 N - N^phi)/(b1 - b2),
-// dxux = -(w3 m3' + w4 m4')/(4 cs2 rho), dyuy = -(w3 m3' - w4 m4')/(4 cs2 rho),
-// omega_z = (2 N^phi - (b1 + b2) N)/(b1 - b2).
+// Sec. 4, from the pre-collision non-equilibrium moments (nf: flow, ng: scalar):
+//   d_i phi = -(w_i^phi / c_phi) ng_i;   N = -w5 nf_5 / (rho c);
+//   N^phi = -w5^phi ng_5 / (phi c_phi) - (b1 uy dxphi + b2 ux dyphi) / phi;
+//   dxux = -(w3 nf_3 + w4 nf_4) / (4 c rho),  dyuy = -(w3 nf_3 - w4 nf_4) / (4 c rho);
+//   omega_z = (2 N^phi - (b1 + b2) N) / (b1 - b2);  S_xy = N / 2.
 struct Kin {
   float sxx, sxy, syy, omega;
 };
 
-__device__ __forceinline__ Kin kinematics(const LbParams& P, const Mom& mf, const Mom& mg,
-                                          const Macro& q, const Eq& ef, const Eq& eg) {
+__device__ __forceinline__ Kin kinematics(const LbParams& P, const Neq& nf, const Neq& ng,
+                                          const Macro& q) {
   Kin k;
-  const float m3n = mf.m3 - ef.e3, m4n = mf.m4 - ef.e4, m5n = mf.kxy - ef.e5;
-  const float n1n = mg.kx - eg.e1, n2n = mg.ky - eg.e2, n5n = mg.kxy - eg.e5;
-  const float inv_cs2p = __frcp_rn(P.cs2p);
-  const float dxphi = -P.wg[1] * inv_cs2p * n1n;
-  const float dyphi = -P.wg[2] * inv_cs2p * n2n;
-  const float irho = __frcp_rn(q.rho);
-  const float N = -P.wf[5] * m5n * irho * __frcp_rn(P.cs2);
-  const float diag = -0.25f * irho * __frcp_rn(P.cs2);
-  k.sxx = diag * (P.wf[3] * m3n + P.wf[4] * m4n);
-  k.syy = diag * (P.wf[3] * m3n - P.wf[4] * m4n);
+  const float inv_c = 3.0f;  // 1 / c_s^2 = 1 / c_sphi^2
+  const float dxphi = -P.wg[1] * inv_c * ng.n1;
+  const float dyphi = -P.wg[2] * inv_c * ng.n2;
+  const float N = -P.wf[5] * nf.n5 * q.irho * inv_c;
+  const float diag = -0.25f * q.irho * inv_c;
+  k.sxx = diag * (P.wf[3] * nf.n3 + P.wf[4] * nf.n4);
+  k.syy = diag * (P.wf[3] * nf.n3 - P.wf[4] * nf.n4);
   k.sxy = 0.5f * N;
   if (fabsf(q.phi) >= P.phimin) {
     const float iphi = __frcp_rn(q.phi);
-    const float Nphi = (-P.wg[5] * n5n * inv_cs2p - (P.b1 * q.uy * dxphi + P.b2 * q.ux * dyphi)) * iphi;
+    const float Nphi = (-P.wg[5] * ng.n5 * inv_c - (P.b1 * q.uy * dxphi + P.b2 * q.ux * dyphi)) * iphi;
     k.omega = (2.0f * Nphi - (P.b1 + P.b2) * N) * P.inv_db;
   } else {
     k.omega = __int_as_float(0x7fc00000);  // NaN: the relations need phi != 0

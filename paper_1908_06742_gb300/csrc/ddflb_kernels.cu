@@ -31,14 +31,10 @@ __global__ void __launch_bounds__(256) k_step(LbParams P, const S* __restrict__ 
   if (status != nullptr && status->diverged) return;
   float df[9], dg[9];
   pull<S, BC>(P, fin, gin, x, y, df, dg);
-  Mom mf = moments(df), mg = moments(dg);
+  const Mom mf = moments_flow(df), mg = moments_scalar(dg);
   const Macro q = macro(P, mf, mg);
-  const Eq ef = eq_flow(P, mf.k0, q.rho, mf.kx, mf.ky, q.ux, q.uy);
-  const Eq eg = eq_scalar(P, mg.k0, q.phi, q.ux, q.uy);
-  relax_flow(P, mf, ef);
-  relax_scalar(P, mg, eg);
-  populations(mf, df);
-  populations(mg, dg);
+  relax(P.wf, neq_flow(mf, q), df);
+  relax(P.wg, neq_scalar(P, mg, mf, q), dg);
   const int64_t o = (int64_t)y * P.pitch + x;
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
@@ -56,11 +52,9 @@ __global__ void __launch_bounds__(256) k_fields(LbParams P, const S* __restrict_
   if (x >= P.nx || y >= P.ny) return;
   float df[9], dg[9];
   pull<S, BC>(P, fin, gin, x, y, df, dg);
-  const Mom mf = moments(df), mg = moments(dg);
+  const Mom mf = moments_flow(df), mg = moments_scalar(dg);
   const Macro q = macro(P, mf, mg);
-  const Eq ef = eq_flow(P, mf.k0, q.rho, mf.kx, mf.ky, q.ux, q.uy);
-  const Eq eg = eq_scalar(P, mg.k0, q.phi, q.ux, q.uy);
-  const Kin k = kinematics(P, mf, mg, q, ef, eg);
+  const Kin k = kinematics(P, neq_flow(mf, q), neq_scalar(P, mg, mf, q), q);
   const int64_t o = (int64_t)y * P.nx + x;
   if (out.p[0]) out.p[0][o] = q.rho;
   if (out.p[1]) out.p[1][o] = q.ux;
@@ -101,32 +95,33 @@ __global__ void __launch_bounds__(256) k_init(LbParams P, InitPtrs in, S* __rest
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= P.nx || y >= P.ny) return;
-  const int64_t c = (int64_t)y * P.nx + x, n = (int64_t)P.nx * P.ny;
-  const float rho = in.rho[c], ux = in.ux[c], uy = in.uy[c], phi = in.phi[c];
+  const int64_t c0 = (int64_t)y * P.nx + x, n = (int64_t)P.nx * P.ny;
+  const float rho = in.rho[c0], ux = in.ux[c0], uy = in.uy[c0], phi = in.phi[c0];
   const float k0 = rho - P.rho0, n0 = phi - P.phi0;
-  const float jx = rho * ux, jy = rho * uy;
-  const Eq ef = eq_flow(P, k0, rho, jx, jy, ux, uy);
-  const Eq eg = eq_scalar(P, n0, phi, ux, uy);
-  Mom mf{k0, jx, jy, ef.e3, ef.e4, ef.e5, ef.e6, ef.e7, ef.e8};
-  Mom mg{n0, eg.e1, eg.e2, eg.e3, eg.e4, eg.e5, eg.e6, eg.e7, eg.e8};
+  const float jx = rho * ux, jy = rho * uy, px = phi * ux, py = phi * uy;
+  const float c = 1.0f / 3.0f, uxx = ux * ux, uyy = uy * uy, usq = uxx + uyy;
+  // equilibrium moments, Eqs. (eqmrawmoment), (eqmrawmoment_CDE), deviation form
+  float m3 = 2.0f * c * k0 + rho * usq, m4 = rho * (uxx - uyy), m5 = jx * uy;
+  float e1 = px, e2 = py, e3 = 2.0f * c * n0 + phi * usq, e4 = phi * (uxx - uyy), e5 = px * uy;
   if (in.grads) {
     // Chapman-Enskog non-equilibrium parts: Eqs. (strainratexxpyy)-(strainratexy)
     // for the flow; Eqs. (1stnoneqmmomentx_CDE), (1stnoneqmmomenty_CDE),
     // (offdiagonal2ndnoneqmmoment_CDE) for the scalar.
-    const float dxux = in.grads[c], dyux = in.grads[n + c];
-    const float dxuy = in.grads[2 * n + c], dyuy = in.grads[3 * n + c];
-    const float dxph = in.grads[4 * n + c], dyph = in.grads[5 * n + c];
-    mf.m3 += -2.0f * P.cs2 * rho / P.wf[3] * (dxux + dyuy);
-    mf.m4 += -2.0f * P.cs2 * rho / P.wf[4] * (dxux - dyuy);
-    mf.kxy += -P.cs2 * rho / P.wf[5] * (dxuy + dyux);
-    mg.kx += -P.cs2p / P.wg[1] * dxph;
-    mg.ky += -P.cs2p / P.wg[2] * dyph;
-    mg.kxy += -P.cs2p / P.wg[5] *
-              (phi * (P.b1 * dxuy + P.b2 * dyux) + P.b1 * uy * dxph + P.b2 * ux * dyph);
+    const float dxux = in.grads[c0], dyux = in.grads[n + c0];
+    const float dxuy = in.grads[2 * n + c0], dyuy = in.grads[3 * n + c0];
+    const float dxph = in.grads[4 * n + c0], dyph = in.grads[5 * n + c0];
+    m3 += -2.0f * c * rho / P.wf[3] * (dxux + dyuy);
+    m4 += -2.0f * c * rho / P.wf[4] * (dxux - dyuy);
+    m5 += -c * rho / P.wf[5] * (dxuy + dyux);
+    e1 += -c / P.wg[1] * dxph;
+    e2 += -c / P.wg[2] * dyph;
+    e5 += -c / P.wg[5] * (phi * (P.b1 * dxuy + P.b2 * dyux) + P.b1 * uy * dxph + P.b2 * ux * dyph);
   }
   float df[9], dg[9];
-  populations(mf, df);
-  populations(mg, dg);
+  populations(k0, jx, jy, m3, m4, m5, jy * (c + uxx), jx * (c + uyy),
+              c * c * k0 + rho * (c * usq + uxx * uyy), df);
+  populations(n0, e1, e2, e3, e4, e5, py * (P.b1 * c + uxx), px * (P.b2 * c + uyy),
+              c * c * n0 + phi * (c * usq + uxx * uyy), dg);
   constexpr int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
   constexpr int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
   constexpr int opp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
@@ -177,7 +172,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(LbParams P, const S* 
     const int y = (int)(c / P.nx), x = (int)(c - (int64_t)y * P.nx);
     float df[9], dg[9];
     pull<S, BC>(P, fin, gin, x, y, df, dg);
-    const Mom mf = moments(df), mg = moments(dg);
+    const Mom mf = moments_flow(df), mg = moments_scalar(dg);
     const Macro q = macro(P, mf, mg);
     s[0] += (double)mf.k0;
     s[1] += (double)mg.k0;
