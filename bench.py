@@ -211,14 +211,15 @@ def traffic_per_launch(args, n_cells):
     try:
         with open(path) as f:
             d = json.load(f)
-        from paper_1908_06742_gb300 import build as B
         import hashlib
-        h = hashlib.sha256()
-        for s in sorted(os.listdir(B.CSRC)):
-            with open(os.path.join(B.CSRC, s), "rb") as fh:
-                h.update(fh.read())
         e = d.get(f"k_step_{args.storage}")
-        if not e or e.get("source_sha256") != h.hexdigest():
+        if not e:
+            return None
+        h = hashlib.sha256()
+        for s in e["source_files"]:
+            with open(os.path.join(ROOT, s), "rb") as fh:
+                h.update(fh.read())
+        if e.get("source_sha256") != h.hexdigest():
             return None
         return e["dram_bytes_per_cell"] * n_cells
     except Exception:
