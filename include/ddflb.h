@@ -164,6 +164,31 @@ size_t ddflb_state_bytes(const ddflb_ctx* c);
 ddflb_status ddflb_get_state(ddflb_ctx* c, void* dev_dst, size_t bytes, int64_t* step);
 ddflb_status ddflb_set_state(ddflb_ctx* c, const void* dev_src, size_t bytes, int64_t step);
 
+/* ddflb_reduce_noalloc - the paper has no counterpart; this exists for
+ * callers that cannot allocate device memory where they need the reductions
+ * (loops where cudaMalloc is forbidden, plug-ins handed only existing
+ * buffers).  It runs the same reduction as ddflb_stats / the residual checks
+ * of ddflb_step on a raw state buffer (the layout ddflb_get_state writes for
+ * parameters *p) and allocates nothing: its scratch (block partial sums, a
+ * status block and a velocity snapshot) is a file-scope device array of the
+ * library, sized for at most DDFLB_NOALLOC_MAX_NODES nodes (about 8.4 MB,
+ * held by every GPU that loads the library until the process exits).
+ *   mode bit 1: also compute the residual |u - u_snap|_2 / |u|_2 against the
+ *               snapshot stored by an earlier call (EINVAL if none of this
+ *               grid size was stored on this device);
+ *   mode bit 2: store this state's velocity as the new snapshot.
+ * dev_out: 4 device doubles (mass, scalar, sum |u|^2, residual or NaN).
+ * Asynchronous on cuda_stream.  The first call on a device, with that device
+ * current, looks up the scratch address (not capturable): make it before any
+ * stream capture.  All calls on a device share the scratch and it keeps the
+ * last call's snapshot; calls that overlap on the GPU (other streams, other
+ * threads) race on it.  Errors: EINVAL (parameters, sizes beyond the maximum,
+ * NULL pointers, missing snapshot), ECUDA. */
+#define DDFLB_NOALLOC_MAX_NODES (1 << 20)
+ddflb_status ddflb_reduce_noalloc(const ddflb_params* p, const void* dev_state,
+                                  size_t state_bytes, int32_t mode, double* dev_out,
+                                  void* cuda_stream);
+
 /* Release the handle (host memory only; the workspace stays the caller's). */
 ddflb_status ddflb_destroy(ddflb_ctx* c);
 

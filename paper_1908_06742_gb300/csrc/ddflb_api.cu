@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -397,3 +398,97 @@ const char* ddflb_last_error(void) { return g_err.c_str(); }
 const char* ddflb_version(void) { return "ddflb 0.1 (sm_103a)"; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Reductions without any device allocation (no counterpart in the paper).
+//
+// For callers that cannot allocate device memory at the point of the call: code
+// paths where cudaMalloc is forbidden or unavailable (real-time loops, callbacks
+// of a framework that owns all device memory, plug-ins handed only pre-existing
+// buffers).  The scratch the reduction needs -- block partial sums, a status
+// block and the velocity snapshot for the residual -- lives in one file-scope
+// device array instead of a caller workspace.  Every GPU that loads this
+// library holds that array (about 8.4 MB) until the process exits.
+namespace {
+
+struct NoallocScratch {
+  double partials[kReduceBlocks * 4];
+  DevStatus status;
+  float uprev[2 * DDFLB_NOALLOC_MAX_NODES];
+};
+
+__device__ __align__(256) NoallocScratch g_noalloc_scratch;
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+NoallocScratch* g_noalloc_addr[kMaxDevices];     // device address, per device ordinal
+int64_t g_noalloc_snapshot_nodes[kMaxDevices];    // node count of the stored snapshot (0: none)
+
+// Turns the status block into (mass, scalar, sum |u|^2, residual).
+__global__ void k_noalloc_out(const DevStatus* st, double cells, double rho0, double phi0,
+                              int mode, double* out) {
+  if (threadIdx.x != 0) return;
+  out[0] = cells * rho0 + st->mass_dev;
+  out[1] = cells * phi0 + st->scalar_dev;
+  out[2] = st->u2;
+  out[3] = (mode & 1) ? st->residual : __longlong_as_double(0x7ff8000000000000LL);
+}
+
+}  // namespace
+
+extern "C" ddflb_status ddflb_reduce_noalloc(const ddflb_params* p, const void* dev_state,
+                                             size_t state_bytes, int32_t mode, double* dev_out,
+                                             void* cuda_stream) {
+  ddflb_status s = validate(p);
+  if (s != DDFLB_OK) return s;
+  if (!dev_state || !dev_out) return fail(DDFLB_EINVAL, "NULL state or output");
+  if (mode < 0 || mode > 3) return fail(DDFLB_EINVAL, "mode %d not in 0..3", mode);
+  const int64_t nodes = (int64_t)p->nx * p->ny;
+  if (nodes > DDFLB_NOALLOC_MAX_NODES)
+    return fail(DDFLB_EINVAL,
+                "grid %d x %d has %lld nodes; ddflb_reduce_noalloc holds scratch for at most %d",
+                p->nx, p->ny, (long long)nodes, DDFLB_NOALLOC_MAX_NODES);
+  const Layout lay = layout(p);
+  if (state_bytes < lay.pops_bytes)
+    return fail(DDFLB_EINVAL, "state buffer %zu bytes < %zu", state_bytes, lay.pops_bytes);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return fail(DDFLB_EINVAL, "device ordinal %d too large", dev);
+  NoallocScratch* scratch = nullptr;
+  {
+    // First call on a device (with that device current): look up the address of
+    // the scratch array.  That lookup is not capturable, so the first call on a
+    // device must come before any stream capture.
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+      void* ptr = nullptr;
+      e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-allocation scratch)");
+      g_noalloc_addr[dev] = (NoallocScratch*)ptr;
+    }
+    scratch = g_noalloc_addr[dev];
+    if ((mode & 1) && g_noalloc_snapshot_nodes[dev] != nodes)
+      return fail(DDFLB_EINVAL, "no velocity snapshot of a %lld-node grid stored on device %d",
+                  (long long)nodes, dev);
+    if (mode & 2) g_noalloc_snapshot_nodes[dev] = nodes;
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  Launch L;
+  L.P = make_lb(p, lay.pitch);
+  L.P_bc = p->bc;
+  L.storage = p->storage;
+  L.block = dim3(128, 1, 1);
+  L.stream = st;
+  // the status block keeps the last call's contents: clear it (diverged flag, residual)
+  e = cudaMemsetAsync(&scratch->status, 0, sizeof(DevStatus), st);
+  if (e != cudaSuccess) return cuda_fail(e, "no-allocation status clear");
+  const char* f = (const char*)dev_state;
+  const char* g = f + 9 * (size_t)lay.pitch * p->ny * elem_size(p->storage);
+  e = launch_reduce(L, f, g, scratch->uprev, mode, scratch->partials, &scratch->status);
+  if (e != cudaSuccess) return cuda_fail(e, "no-allocation reduce");
+  k_noalloc_out<<<1, 32, 0, st>>>(&scratch->status, (double)nodes, p->rho0, p->phi0, mode,
+                                  dev_out);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? DDFLB_OK : cuda_fail(e, "no-allocation output");
+}

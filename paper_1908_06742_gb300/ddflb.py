@@ -70,6 +70,8 @@ SIGNATURES = {
     "ddflb_get_state": (ctypes.c_int, [_VP, _FP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int64)]),
     "ddflb_set_state": (ctypes.c_int, [_VP, _FP, ctypes.c_size_t, ctypes.c_int64]),
     "ddflb_destroy": (ctypes.c_int, [_VP]),
+    "ddflb_reduce_noalloc": (ctypes.c_int, [ctypes.POINTER(Params), _FP, ctypes.c_size_t,
+                                            ctypes.c_int32, _FP, _VP]),
     "ddflb_last_error": (ctypes.c_char_p, []),
     "ddflb_version": (ctypes.c_char_p, []),
 }
@@ -165,6 +167,21 @@ def workspace_bytes(cfg: Config) -> int:
     if n == 0:
         _check(EINVAL)
     return n
+
+
+NOALLOC_MAX_NODES = 1 << 20
+
+
+def reduce_noalloc(cfg: Config, state, mode: int, out, stream=None):
+    """ddflb_reduce_noalloc on a raw state tensor (as from Lattice.get_state):
+    writes (mass, scalar, sum |u|^2, residual) into the 4-double device tensor
+    ``out`` without allocating device memory."""
+    import torch
+    p = cfg.to_c()
+    st = stream or torch.cuda.current_stream()
+    _check(load().ddflb_reduce_noalloc(ctypes.byref(p), state.data_ptr(), state.numel(),
+                                       int(mode), out.data_ptr(), st.cuda_stream))
+    return out
 
 
 def _dptr(t) -> Optional[int]:
