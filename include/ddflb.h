@@ -192,6 +192,57 @@ ddflb_status ddflb_reduce_noalloc(const ddflb_params* p, const void* dev_state,
 /* Release the handle (host memory only; the workspace stays the caller's). */
 ddflb_status ddflb_destroy(ddflb_ctx* c);
 
+/* ---------------------------------------------------------------------------
+ * Batched lattices: n independent lattice pairs (each its own ddflb_params:
+ * size, boundary kind, rates, lid) advanced together.  Each chunk of steps is
+ * one persistent cooperative launch that walks a flattened tile list of all
+ * instances, with a device-wide barrier between time steps whose waits are
+ * bounded in time (a wait that runs out ends the launch; *_stats then returns
+ * ETIMEOUT).  A chunk launch is captured once as a CUDA graph and replayed.
+ * All instances share storage precision and check_every.  Every check_every
+ * steps each instance's residual r = |u(t)-u(t-1)|/|u(t)| is reduced in a
+ * fixed order; an instance whose r falls below the tolerance (converged) or
+ * whose sums are not finite (diverged) is frozen from then on. */
+#define DDFLB_INST_CONVERGED 1
+#define DDFLB_INST_DIVERGED 2
+typedef struct ddflb_batch ddflb_batch;
+
+/* Workspace bytes for n instances with parameters p[0..n-1] (0 if invalid). */
+size_t ddflb_batch_workspace_bytes(int32_t n, const ddflb_params* p);
+/* Carve the batch out of dev_workspace (256-byte aligned, caller-owned) and
+ * upload its tile list (synchronises the stream once).  Default tiles 128 x 1,
+ * as many co-resident CTAs per SM as fit.  Errors: EINVAL, ENOMEM, ECUDA. */
+ddflb_status ddflb_batch_create(int32_t n, const ddflb_params* p, void* dev_workspace,
+                                size_t bytes, void* cuda_stream, ddflb_batch** out);
+/* Tolerance for the convergence freeze (0 = never freeze on convergence),
+ * steps per persistent launch, and the barrier wait limit in seconds. */
+ddflb_status ddflb_batch_set_run(ddflb_batch* b, double tol, int32_t steps_per_launch,
+                                 double barrier_timeout_s);
+/* Tile shape (32x4, 64x2, 128x1, 32x8, 64x4, 128x2, 256x1) and CTAs per SM
+ * (0 = as many as fit); rebuilds the tile list.  Used by the autotuner. */
+ddflb_status ddflb_batch_set_tiles(ddflb_batch* b, int32_t tile_x, int32_t tile_y,
+                                   int32_t blocks_per_sm);
+ddflb_status ddflb_batch_get_tiles(const ddflb_batch* b, int32_t* tile_x, int32_t* tile_y,
+                                   int32_t* blocks_per_sm);
+/* Initialise instance i at the batch's current time from device fields, as
+ * ddflb_init (clears its converged/diverged flags). */
+ddflb_status ddflb_batch_init(ddflb_batch* b, int32_t i, const float* rho, const float* ux,
+                              const float* uy, const float* phi, const float* grads);
+/* Advance all active instances n steps (asynchronous). */
+ddflb_status ddflb_batch_step(ddflb_batch* b, int64_t n);
+/* Local kinematics of instance i's current state, as ddflb_fields. */
+ddflb_status ddflb_batch_fields(ddflb_batch* b, int32_t i, float* rho, float* ux, float* uy,
+                                float* phi, float* sxx, float* sxy, float* syy, float* omega);
+/* Per-instance host arrays (any may be NULL): last residual, flags, the state
+ * time at which the residual first fell below tol (-1: not yet) and the state
+ * time of the current state.  Synchronises; ETIMEOUT if a barrier wait ran out. */
+ddflb_status ddflb_batch_stats(ddflb_batch* b, double* residual, int32_t* flags,
+                               int64_t* steps_to_tol, int64_t* state_time);
+/* Test hook: CTA `block` of the next launch skips its first barrier so that the
+ * others' bounded waits run out (-1 disables).  Never faults or hangs. */
+ddflb_status ddflb_batch_debug_skip_barrier(ddflb_batch* b, int32_t block);
+ddflb_status ddflb_batch_destroy(ddflb_batch* b);
+
 /* Message of the last error on the calling thread ("" if none). */
 const char* ddflb_last_error(void);
 

@@ -149,6 +149,11 @@ LbParams make_lb(const ddflb_params* p, int pitch) {
 
 }  // namespace
 
+namespace ddflb {
+void set_error(const char* msg) { g_err = msg; }
+LbParams make_lbparams(const ddflb_params* p, int pitch) { return make_lb(p, pitch); }
+}  // namespace ddflb
+
 struct ddflb_ctx {
   ddflb_params p;
   Layout lay;

@@ -1,0 +1,681 @@
+// Batched persistent step: many independent lattice pairs of uneven sizes and
+// parameters advance together in one cooperative launch per chunk of steps.
+//
+// Work list: every instance is cut into tiles of tile_x * tile_y nodes; the
+// flattened tile list is walked round-robin by all CTAs of a grid sized to the
+// number of co-resident CTAs (cooperative launch), so uneven instance sizes
+// balance out.  Between time steps the CTAs meet at a device-wide barrier whose
+// waits are bounded in time: a wait that runs out records an error and every
+// CTA leaves the kernel, which the host reports as DDFLB_ETIMEOUT.
+//
+// Every check_every steps the step kernel also accumulates, per tile, the sums
+// for the velocity residual r = |u(t) - u(t-1)|_2 / |u(t)|_2 and the mass;
+// after a barrier each instance's tiles are reduced in a fixed order
+// (deterministic), and an instance whose residual fell below the tolerance or
+// whose sums are not finite is frozen (its tiles are skipped from then on).
+//
+// The chunk launch reads the current step from device memory, so one captured
+// CUDA graph of the launch replays for every chunk.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/ddflb.h"
+#include "ddflb_device.cuh"
+#include "ddflb_internal.h"
+
+namespace ddflb {
+
+struct BatchInst {
+  LbParams P;
+  void* buf[2];  // f planes; g planes follow 9 planes later
+  float* uprev;  // 2 planes [ny][nx]
+  int64_t goff;  // element offset of the g planes from the f planes
+  int32_t tile_begin, tile_end;
+  int32_t bc;
+  int32_t pad;
+};
+
+struct BatchStatus {
+  double residual;
+  double u2;
+  double mass_dev;
+  int64_t steps_to_tol;  // state time at which the residual first fell below tol (-1: not yet)
+  int64_t state_time;    // state time of the instance's current state when frozen
+  int32_t flags;         // DDFLB_INST_CONVERGED | DDFLB_INST_DIVERGED
+  int32_t pad;
+};
+
+struct BatchSync {
+  unsigned count;
+  unsigned gen;
+  int err;       // 1: a barrier wait ran out
+  int pad;
+  int64_t step;  // state time of all active instances
+  int64_t pad2[5];
+};
+
+struct BatchArgs {
+  const BatchInst* inst;
+  int ninst;
+  const int4* tiles;
+  int ntiles;
+  int tile_x, tile_y;
+  int nsteps;
+  int check_every;
+  double tol;
+  double* part;  // 3 doubles per tile
+  BatchStatus* ist;
+  BatchSync* sync;
+  long long timeout_ns;
+  int skip_block;  // test hook: this CTA never arrives at the first barrier (-1: none)
+};
+
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Device-wide barrier for a cooperative grid (all CTAs co-resident).  Returns
+// false if the barrier failed (this or another CTA timed out).
+__device__ bool grid_barrier(BatchSync* s, long long timeout_ns) {
+  __syncthreads();
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = &s->gen;
+    volatile int* err = &s->err;
+    const unsigned g = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&s->count, 1u);
+    if (arrived == gridDim.x - 1) {
+      s->count = 0;
+      __threadfence();
+      atomicAdd(&s->gen, 1u);
+    } else {
+      const unsigned long long t0 = now_ns();
+      unsigned spins = 0;
+      while (*gen == g && *err == 0) {
+        __nanosleep(64);
+        if ((++spins & 255u) == 0 && (long long)(now_ns() - t0) > timeout_ns) {
+          atomicExch(&s->err, 1);
+          break;
+        }
+        if (spins > (1u << 30)) {  // hard bound independent of the timer
+          atomicExch(&s->err, 1);
+          break;
+        }
+      }
+    }
+    __threadfence();
+    ok = (*err == 0);
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <typename S, int BC>
+__device__ __forceinline__ void batch_cell(const LbParams& P, const BatchInst& I, int src, int x,
+                                           int y, bool snap, bool check, double acc[3]) {
+  const S* fin = (const S*)I.buf[src];
+  const S* gin = fin + I.goff;
+  S* fout = (S*)I.buf[src ^ 1];
+  S* gout = fout + I.goff;
+  float df[9], dg[9];
+  pull<S, BC>(P, fin, gin, x, y, df, dg);
+  const Mom mf = moments_flow(df), mg = moments_scalar(dg);
+  const Macro q = macro(P, mf, mg);
+  relax(P.wf, neq_flow(mf, q), df);
+  relax(P.wg, neq_scalar(P, mg, mf, q), dg);
+  const int64_t o = (int64_t)y * P.pitch + x;
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    Codec<S>::store(fout + a * P.plane + o, df[a], P.sf);
+    Codec<S>::store(gout + a * P.plane + o, dg[a], P.sg);
+  }
+  if (check || snap) {
+    const int64_t c = (int64_t)y * P.nx + x, n = (int64_t)P.nx * P.ny;
+    if (check) {
+      const double ex = (double)q.ux - I.uprev[c], ey = (double)q.uy - I.uprev[n + c];
+      acc[0] += (double)q.ux * q.ux + (double)q.uy * q.uy;
+      acc[1] += ex * ex + ey * ey;
+      acc[2] += (double)mf.k0;
+    }
+    if (snap) {
+      I.uprev[c] = q.ux;
+      I.uprev[n + c] = q.uy;
+    }
+  }
+}
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < nw; ++k) t += sh[k];
+  return t;  // valid in thread 0
+}
+
+template <typename S>
+__global__ void __launch_bounds__(256) k_batch(BatchArgs A) {
+  __shared__ BatchInst sI;
+  __shared__ double sh[8];
+  __shared__ int sActive;
+  const int64_t t0 = A.sync->step;
+  const LbParams& sP = sI.P;
+  // each CTA owns a contiguous range of tiles: instance parameters are staged
+  // in shared memory once per instance change, not once per tile
+  const int per = (A.ntiles + gridDim.x - 1) / gridDim.x;
+  const int tb = blockIdx.x * per, te = min(A.ntiles, tb + per);
+  int cur = -1;
+  for (int s = 0; s < A.nsteps; ++s) {
+    const int64_t t = t0 + s;
+    const int src = (int)(t & 1);
+    const bool check = A.check_every > 0 && t > 0 && t % A.check_every == 0;
+    const bool snap = A.check_every > 0 && t % A.check_every == A.check_every - 1;
+    for (int tile = tb; tile < te; ++tile) {
+      const int4 T = A.tiles[tile];
+      if (T.x != cur) {
+        __syncthreads();
+        const int* srcw = (const int*)(A.inst + T.x);
+        int* dstw = (int*)&sI;
+        for (int w = threadIdx.x; w < (int)(sizeof(BatchInst) / 4); w += blockDim.x) dstw[w] = srcw[w];
+        if (threadIdx.x == 0) sActive = __ldcg(&A.ist[T.x].flags) == 0;
+        cur = T.x;
+        __syncthreads();
+      }
+      if (!sActive) continue;
+      const int x = T.y + threadIdx.x % A.tile_x, y = T.z + threadIdx.x / A.tile_x;
+      double acc[3] = {0.0, 0.0, 0.0};
+      if (x < sP.nx && y < sP.ny) {
+        switch (sI.bc) {
+          case BC_PERIODIC: batch_cell<S, BC_PERIODIC>(sP, sI, src, x, y, snap, check, acc); break;
+          case BC_CAVITY: batch_cell<S, BC_CAVITY>(sP, sI, src, x, y, snap, check, acc); break;
+          default: batch_cell<S, BC_CHANNEL>(sP, sI, src, x, y, snap, check, acc);
+        }
+      }
+      if (check) {
+        for (int k = 0; k < 3; ++k) {
+          const double v = block_sum(acc[k], sh);
+          if (threadIdx.x == 0) A.part[3 * (int64_t)tile + k] = v;
+        }
+      }
+    }
+    if (check) {
+      if (!grid_barrier(A.sync, A.timeout_ns)) return;
+      // per-instance fixed-order reduction of the tile sums
+      for (int i = blockIdx.x; i < A.ninst; i += gridDim.x) {
+        if (__ldcg(&A.ist[i].flags) != 0) continue;
+        const int b = A.inst[i].tile_begin, e = A.inst[i].tile_end;
+        double v[3];
+        for (int k = 0; k < 3; ++k) {
+          double a = 0.0;
+          for (int j = b + threadIdx.x; j < e; j += blockDim.x) a += __ldcg(&A.part[3 * (int64_t)j + k]);
+          v[k] = block_sum(a, sh);
+        }
+        if (threadIdx.x == 0) {
+          BatchStatus& st = A.ist[i];
+          st.u2 = v[0];
+          st.mass_dev = v[2];
+          st.residual = v[0] > 0.0 ? sqrt(v[1] / v[0]) : 0.0;
+          if (!isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2])) {
+            st.flags = DDFLB_INST_DIVERGED;
+            st.state_time = t + 1;
+          } else if (A.tol > 0.0 && st.residual < A.tol) {
+            st.flags = DDFLB_INST_CONVERGED;
+            st.steps_to_tol = t;
+            st.state_time = t + 1;
+          }
+        }
+      }
+      cur = -1;  // re-read the activity flags
+    }
+    if (s == 0 && (int)blockIdx.x == A.skip_block) return;  // test hook: never arrive
+    if (!grid_barrier(A.sync, A.timeout_ns)) return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) A.sync->step = t0 + A.nsteps;
+}
+
+}  // namespace ddflb
+
+using namespace ddflb;
+
+namespace {
+
+thread_local std::string g_berr;
+
+ddflb_status bfail(ddflb_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  set_error(buf);
+  return s;
+}
+
+ddflb_status bcuda(cudaError_t e, const char* where) {
+  return bfail(DDFLB_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+constexpr size_t kAl = 256;
+size_t al(size_t v) { return (v + kAl - 1) / kAl * kAl; }
+size_t esz(int storage) { return storage == DDFLB_FP32 ? 4 : 2; }
+int bpitch(int nx) { return (nx + 31) / 32 * 32; }
+
+const int kShapes[][2] = {{32, 4}, {64, 2}, {128, 1}, {32, 8}, {64, 4}, {128, 2}, {256, 1}};
+constexpr int kNumShapes = 7;
+
+struct BLayout {
+  std::vector<size_t> off_buf0, off_buf1, off_uprev;
+  size_t off_inst, off_tiles, off_part, off_status, off_sync, total;
+  int max_tiles;
+};
+
+int count_tiles(int n, const ddflb_params* p, int tx, int ty) {
+  int64_t t = 0;
+  for (int i = 0; i < n; ++i) t += (int64_t)((p[i].nx + tx - 1) / tx) * ((p[i].ny + ty - 1) / ty);
+  return t > (1 << 30) ? -1 : (int)t;
+}
+
+BLayout blayout(int n, const ddflb_params* p) {
+  BLayout L;
+  size_t o = 0;
+  for (int i = 0; i < n; ++i) {
+    const size_t plane = (size_t)bpitch(p[i].nx) * p[i].ny;
+    const size_t bytes = al(18 * plane * esz(p[i].storage));
+    L.off_buf0.push_back(o); o += bytes;
+    L.off_buf1.push_back(o); o += bytes;
+    L.off_uprev.push_back(o); o += al(2 * (size_t)p[i].nx * p[i].ny * sizeof(float));
+  }
+  int mt = 0;
+  for (int k = 0; k < kNumShapes; ++k) mt = std::max(mt, count_tiles(n, p, kShapes[k][0], kShapes[k][1]));
+  L.max_tiles = mt;
+  L.off_inst = o; o += al(n * sizeof(BatchInst));
+  L.off_tiles = o; o += al((size_t)mt * sizeof(int4));
+  L.off_part = o; o += al((size_t)mt * 3 * sizeof(double));
+  L.off_status = o; o += al(n * sizeof(BatchStatus));
+  L.off_sync = o; o += al(sizeof(BatchSync));
+  L.total = o;
+  return L;
+}
+
+}  // namespace
+
+struct ddflb_batch {
+  int n;
+  std::vector<ddflb_params> p;
+  std::vector<LbParams> lp;
+  BLayout lay;
+  char* ws;
+  cudaStream_t stream;
+  int storage;
+  int tile_x, tile_y, blocks_per_sm, grid;
+  int ntiles;
+  int chunk;
+  double tol;
+  long long timeout_ns;
+  int skip_block;
+  int64_t step;  // host mirror of the global state time
+  BatchInst* d_inst;
+  int4* d_tiles;
+  double* d_part;
+  BatchStatus* d_status;
+  BatchSync* d_sync;
+  cudaGraphExec_t graph;
+  int graph_chunk;
+  bool graph_failed;
+};
+
+namespace {
+
+ddflb_status upload_tiles(ddflb_batch* b) {
+  std::vector<int4> tiles;
+  std::vector<BatchInst> inst(b->n);
+  for (int i = 0; i < b->n; ++i) {
+    BatchInst& I = inst[i];
+    std::memset(&I, 0, sizeof I);
+    I.P = b->lp[i];
+    I.buf[0] = b->ws + b->lay.off_buf0[i];
+    I.buf[1] = b->ws + b->lay.off_buf1[i];
+    I.uprev = (float*)(b->ws + b->lay.off_uprev[i]);
+    I.goff = 9 * I.P.plane;
+    I.bc = b->p[i].bc;
+    I.tile_begin = (int)tiles.size();
+    for (int y = 0; y < b->p[i].ny; y += b->tile_y)
+      for (int x = 0; x < b->p[i].nx; x += b->tile_x) tiles.push_back(make_int4(i, x, y, 0));
+    I.tile_end = (int)tiles.size();
+  }
+  b->ntiles = (int)tiles.size();
+  cudaError_t e = cudaMemcpyAsync(b->d_inst, inst.data(), inst.size() * sizeof(BatchInst),
+                                  cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(int4),
+                        cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  return e == cudaSuccess ? DDFLB_OK : bcuda(e, "batch tile upload");
+}
+
+template <typename S>
+void* kernel_ptr() { return (void*)k_batch<S>; }
+
+void* batch_kernel(int storage) {
+  return storage == 0 ? kernel_ptr<float>() : storage == 1 ? kernel_ptr<__half>()
+                                                            : kernel_ptr<__nv_bfloat16>();
+}
+
+ddflb_status configure(ddflb_batch* b, int tx, int ty, int bps) {
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  int occ = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel(b->storage), tx * ty, 0);
+  if (e != cudaSuccess) return bcuda(e, "batch occupancy");
+  if (occ < 1) return bfail(DDFLB_EINVAL, "batch kernel cannot be resident with %d threads", tx * ty);
+  b->tile_x = tx;
+  b->tile_y = ty;
+  b->blocks_per_sm = bps > 0 ? std::min(bps, occ) : occ;
+  b->grid = b->blocks_per_sm * nsm;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  return upload_tiles(b);
+}
+
+BatchArgs args_for(ddflb_batch* b, int nsteps) {
+  BatchArgs A;
+  A.inst = b->d_inst;
+  A.ninst = b->n;
+  A.tiles = b->d_tiles;
+  A.ntiles = b->ntiles;
+  A.tile_x = b->tile_x;
+  A.tile_y = b->tile_y;
+  A.nsteps = nsteps;
+  A.check_every = b->p[0].check_every;
+  A.tol = b->tol;
+  A.part = b->d_part;
+  A.ist = b->d_status;
+  A.sync = b->d_sync;
+  A.timeout_ns = b->timeout_ns;
+  A.skip_block = b->skip_block;
+  return A;
+}
+
+cudaError_t launch_chunk(ddflb_batch* b, cudaStream_t s, int nsteps) {
+  BatchArgs A = args_for(b, nsteps);
+  void* kargs[] = {&A};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(b->grid);
+  cfg.blockDim = dim3(b->tile_x * b->tile_y);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, batch_kernel(b->storage), kargs);
+}
+
+// Capture one chunk launch into a graph (on a private stream) for replay.
+void build_graph(ddflb_batch* b, int nsteps) {
+  if (b->graph_failed) return;
+  cudaStream_t cs;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+    b->graph_failed = true;
+    return;
+  }
+  cudaGraph_t g = nullptr;
+  bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    ok = launch_chunk(b, cs, nsteps) == cudaSuccess;
+    ok = (cudaStreamEndCapture(cs, &g) == cudaSuccess) && ok;
+  }
+  cudaGraphExec_t ex = nullptr;
+  if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  cudaGetLastError();  // clear a capture error, if any
+  if (!ok) {
+    b->graph_failed = true;
+    return;
+  }
+  b->graph = ex;
+  b->graph_chunk = nsteps;
+}
+
+ddflb_status check_sync_error(ddflb_batch* b) {
+  BatchSync h;
+  cudaError_t e = cudaMemcpyAsync(&h, b->d_sync, sizeof h, cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bcuda(e, "batch status");
+  if (h.err) return bfail(DDFLB_ETIMEOUT, "a device-wide barrier wait ran out (step %lld)",
+                          (long long)h.step);
+  return DDFLB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t ddflb_batch_workspace_bytes(int32_t n, const ddflb_params* p) {
+  if (n <= 0 || !p) return 0;
+  for (int i = 0; i < n; ++i) {
+    if (ddflb_workspace_bytes(&p[i]) == 0) return 0;
+    if (p[i].storage != p[0].storage || p[i].check_every != p[0].check_every) {
+      set_error("all instances of a batch share storage and check_every");
+      return 0;
+    }
+  }
+  const BLayout L = blayout(n, p);
+  return L.max_tiles < 0 ? 0 : L.total;
+}
+
+ddflb_status ddflb_batch_create(int32_t n, const ddflb_params* p, void* ws, size_t bytes,
+                                void* stream, ddflb_batch** out) {
+  if (!out) return bfail(DDFLB_EINVAL, "out is NULL");
+  *out = nullptr;
+  const size_t need = ddflb_batch_workspace_bytes(n, p);
+  if (need == 0) return DDFLB_EINVAL;  // message set by the size query
+  if (!ws || (uintptr_t)ws % kAl) return bfail(DDFLB_EINVAL, "workspace NULL or not 256-aligned");
+  if (bytes < need) return bfail(DDFLB_ENOMEM, "workspace %zu bytes < %zu required", bytes, need);
+  ddflb_batch* b = new (std::nothrow) ddflb_batch();
+  if (!b) return bfail(DDFLB_ENOMEM, "host allocation of the handle failed");
+  b->n = n;
+  b->p.assign(p, p + n);
+  b->lay = blayout(n, p);
+  for (int i = 0; i < n; ++i) b->lp.push_back(make_lbparams(&p[i], bpitch(p[i].nx)));
+  b->ws = (char*)ws;
+  b->stream = (cudaStream_t)stream;
+  b->storage = p[0].storage;
+  b->chunk = 500;
+  b->tol = 0.0;
+  b->timeout_ns = 2000000000LL;
+  b->skip_block = -1;
+  b->step = 0;
+  b->d_inst = (BatchInst*)(b->ws + b->lay.off_inst);
+  b->d_tiles = (int4*)(b->ws + b->lay.off_tiles);
+  b->d_part = (double*)(b->ws + b->lay.off_part);
+  b->d_status = (BatchStatus*)(b->ws + b->lay.off_status);
+  b->d_sync = (BatchSync*)(b->ws + b->lay.off_sync);
+  b->graph = nullptr;
+  b->graph_failed = false;
+  cudaError_t e = cudaMemsetAsync(b->d_sync, 0, sizeof(BatchSync), b->stream);
+  if (e != cudaSuccess) {
+    delete b;
+    return bcuda(e, "batch create");
+  }
+  std::vector<BatchStatus> st(n);
+  for (auto& s : st) {
+    std::memset(&s, 0, sizeof s);
+    s.steps_to_tol = -1;
+    s.residual = NAN;
+  }
+  e = cudaMemcpyAsync(b->d_status, st.data(), n * sizeof(BatchStatus), cudaMemcpyHostToDevice,
+                      b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) {
+    delete b;
+    return bcuda(e, "batch create");
+  }
+  ddflb_status s = configure(b, 128, 1, 0);
+  if (s != DDFLB_OK) {
+    delete b;
+    return s;
+  }
+  *out = b;
+  return DDFLB_OK;
+}
+
+ddflb_status ddflb_batch_set_run(ddflb_batch* b, double tol, int32_t steps_per_launch,
+                                 double barrier_timeout_s) {
+  if (!b) return bfail(DDFLB_EINVAL, "NULL batch");
+  if (!(tol >= 0) || steps_per_launch < 1 || !(barrier_timeout_s > 0 && barrier_timeout_s <= 60))
+    return bfail(DDFLB_EINVAL, "tol >= 0, steps_per_launch >= 1, timeout in (0, 60] s");
+  b->tol = tol;
+  b->chunk = steps_per_launch;
+  b->timeout_ns = (long long)(barrier_timeout_s * 1e9);
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  return DDFLB_OK;
+}
+
+ddflb_status ddflb_batch_set_tiles(ddflb_batch* b, int32_t tile_x, int32_t tile_y,
+                                   int32_t blocks_per_sm) {
+  if (!b) return bfail(DDFLB_EINVAL, "NULL batch");
+  bool ok = false;
+  for (int k = 0; k < kNumShapes; ++k) ok = ok || (kShapes[k][0] == tile_x && kShapes[k][1] == tile_y);
+  if (!ok) return bfail(DDFLB_EINVAL, "tile %d x %d is not one of the supported shapes", tile_x, tile_y);
+  if (blocks_per_sm < 0) return bfail(DDFLB_EINVAL, "blocks_per_sm < 0");
+  return configure(b, tile_x, tile_y, blocks_per_sm);
+}
+
+ddflb_status ddflb_batch_get_tiles(const ddflb_batch* b, int32_t* tile_x, int32_t* tile_y,
+                                   int32_t* blocks_per_sm) {
+  if (!b) return bfail(DDFLB_EINVAL, "NULL batch");
+  if (tile_x) *tile_x = b->tile_x;
+  if (tile_y) *tile_y = b->tile_y;
+  if (blocks_per_sm) *blocks_per_sm = b->blocks_per_sm;
+  return DDFLB_OK;
+}
+
+ddflb_status ddflb_batch_init(ddflb_batch* b, int32_t i, const float* rho, const float* ux,
+                              const float* uy, const float* phi, const float* grads) {
+  if (!b || i < 0 || i >= b->n || !rho || !ux || !uy || !phi)
+    return bfail(DDFLB_EINVAL, "bad batch, instance index or NULL field");
+  const ddflb_params& p = b->p[i];
+  if (grads && (p.omega_f[3] <= 0 || p.omega_f[4] <= 0 || p.omega_f[5] <= 0 ||
+                p.omega_g[1] <= 0 || p.omega_g[2] <= 0 || p.omega_g[5] <= 0))
+    return bfail(DDFLB_EINVAL, "gradient initialisation needs w3, w4, w5, w1^phi, w2^phi, w5^phi > 0");
+  Launch L;
+  L.P = b->lp[i];
+  L.P_bc = p.bc;
+  L.storage = p.storage;
+  L.block = dim3(128, 1, 1);
+  L.stream = b->stream;
+  InitPtrs in{rho, ux, uy, phi, grads};
+  // the instance joins at the batch's current state time
+  const size_t off = (b->step & 1) ? b->lay.off_buf1[i] : b->lay.off_buf0[i];
+  char* f = b->ws + off;
+  char* g = f + 9 * (size_t)L.P.plane * esz(p.storage);
+  cudaError_t e = launch_init(L, in, f, g);
+  if (e != cudaSuccess) return bcuda(e, "batch init");
+  BatchStatus s;
+  std::memset(&s, 0, sizeof s);
+  s.steps_to_tol = -1;
+  s.residual = NAN;
+  e = cudaMemcpyAsync(b->d_status + i, &s, sizeof s, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  return e == cudaSuccess ? DDFLB_OK : bcuda(e, "batch init status");
+}
+
+ddflb_status ddflb_batch_step(ddflb_batch* b, int64_t n) {
+  if (!b) return bfail(DDFLB_EINVAL, "NULL batch");
+  if (n < 0) return bfail(DDFLB_EINVAL, "n < 0");
+  int64_t left = n;
+  while (left > 0) {
+    const int k = (int)std::min<int64_t>(left, b->chunk);
+    if (k == b->chunk && !b->graph) build_graph(b, k);
+    cudaError_t e;
+    if (k == b->chunk && b->graph)
+      e = cudaGraphLaunch(b->graph, b->stream);
+    else
+      e = launch_chunk(b, b->stream, k);
+    if (e != cudaSuccess) return bcuda(e, "batch step launch");
+    left -= k;
+    b->step += k;
+  }
+  return DDFLB_OK;
+}
+
+ddflb_status ddflb_batch_fields(ddflb_batch* b, int32_t i, float* rho, float* ux, float* uy,
+                                float* phi, float* sxx, float* sxy, float* syy, float* omega) {
+  if (!b || i < 0 || i >= b->n) return bfail(DDFLB_EINVAL, "bad batch or instance index");
+  BatchStatus s;
+  cudaError_t e = cudaMemcpyAsync(&s, b->d_status + i, sizeof s, cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bcuda(e, "batch fields status");
+  const int64_t t = s.flags ? s.state_time : b->step;
+  Launch L;
+  L.P = b->lp[i];
+  L.P_bc = b->p[i].bc;
+  L.storage = b->p[i].storage;
+  L.block = dim3(128, 1, 1);
+  L.stream = b->stream;
+  const char* f = b->ws + ((t & 1) ? b->lay.off_buf1[i] : b->lay.off_buf0[i]);
+  const char* g = f + 9 * (size_t)L.P.plane * esz(b->p[i].storage);
+  FieldPtrs fp{{rho, ux, uy, phi, sxx, sxy, syy, omega}};
+  e = launch_fields(L, f, g, fp);
+  return e == cudaSuccess ? DDFLB_OK : bcuda(e, "batch fields");
+}
+
+ddflb_status ddflb_batch_stats(ddflb_batch* b, double* residual, int32_t* flags,
+                               int64_t* steps_to_tol, int64_t* state_time) {
+  if (!b) return bfail(DDFLB_EINVAL, "NULL batch");
+  std::vector<BatchStatus> h(b->n);
+  cudaError_t e = cudaMemcpyAsync(h.data(), b->d_status, b->n * sizeof(BatchStatus),
+                                  cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bcuda(e, "batch stats");
+  for (int i = 0; i < b->n; ++i) {
+    if (residual) residual[i] = h[i].residual;
+    if (flags) flags[i] = h[i].flags;
+    if (steps_to_tol) steps_to_tol[i] = h[i].steps_to_tol;
+    if (state_time) state_time[i] = h[i].flags ? h[i].state_time : b->step;
+  }
+  return check_sync_error(b);
+}
+
+ddflb_status ddflb_batch_debug_skip_barrier(ddflb_batch* b, int32_t block) {
+  if (!b) return bfail(DDFLB_EINVAL, "NULL batch");
+  b->skip_block = block;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  return DDFLB_OK;
+}
+
+ddflb_status ddflb_batch_destroy(ddflb_batch* b) {
+  if (b && b->graph) cudaGraphExecDestroy(b->graph);
+  delete b;
+  return DDFLB_OK;
+}
+
+}  // extern "C"

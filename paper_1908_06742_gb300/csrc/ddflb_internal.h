@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/ddflb.h"
 #include "ddflb_device.cuh"
 
 namespace ddflb {
@@ -34,5 +35,9 @@ cudaError_t launch_pops(const Launch& L, const void* fin, const void* gin, float
 cudaError_t launch_init(const Launch& L, const InitPtrs& in, void* fout, void* gout);
 cudaError_t launch_reduce(const Launch& L, const void* fin, const void* gin, float* uprev,
                           int mode, double* partials, DevStatus* st);
+
+// Shared by the single-lattice and batched entry points (ddflb_api.cu).
+void set_error(const char* msg);                     // thread-local ddflb_last_error()
+LbParams make_lbparams(const ddflb_params* p, int pitch);
 
 }  // namespace ddflb

@@ -72,9 +72,23 @@ SIGNATURES = {
     "ddflb_destroy": (ctypes.c_int, [_VP]),
     "ddflb_reduce_noalloc": (ctypes.c_int, [ctypes.POINTER(Params), _FP, ctypes.c_size_t,
                                             ctypes.c_int32, _FP, _VP]),
+    "ddflb_batch_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32, ctypes.POINTER(Params)]),
+    "ddflb_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(Params), _VP,
+                                          ctypes.c_size_t, _VP, ctypes.POINTER(_VP)]),
+    "ddflb_batch_set_run": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_int32, ctypes.c_double]),
+    "ddflb_batch_set_tiles": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "ddflb_batch_get_tiles": (ctypes.c_int, [_VP] + [ctypes.POINTER(ctypes.c_int32)] * 3),
+    "ddflb_batch_init": (ctypes.c_int, [_VP, ctypes.c_int32, _FP, _FP, _FP, _FP, _FP]),
+    "ddflb_batch_step": (ctypes.c_int, [_VP, ctypes.c_int64]),
+    "ddflb_batch_fields": (ctypes.c_int, [_VP, ctypes.c_int32] + [_FP] * 8),
+    "ddflb_batch_stats": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "ddflb_batch_debug_skip_barrier": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "ddflb_batch_destroy": (ctypes.c_int, [_VP]),
     "ddflb_last_error": (ctypes.c_char_p, []),
     "ddflb_version": (ctypes.c_char_p, []),
 }
+
+INST_CONVERGED, INST_DIVERGED = 1, 2
 
 
 def load(path: str = LIB_PATH):
@@ -278,6 +292,89 @@ class Lattice:
     def close(self):
         if getattr(self, "_h", None):
             self.lib.ddflb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent lattice pairs of uneven sizes advanced together on the GPU
+    (one persistent cooperative launch per chunk of steps)."""
+
+    def __init__(self, cfgs, device=None, stream=None):
+        import torch
+        self.torch = torch
+        self.cfgs = list(cfgs)
+        self.n = len(self.cfgs)
+        self.device = torch.device(device or "cuda")
+        self.lib = load()
+        self._p = (Params * self.n)(*[c.to_c() for c in self.cfgs])
+        nbytes = self.lib.ddflb_batch_workspace_bytes(self.n, self._p)
+        if nbytes == 0:
+            _check(EINVAL)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream or torch.cuda.current_stream(self.device)
+        h = _VP()
+        _check(self.lib.ddflb_batch_create(self.n, self._p, self.workspace.data_ptr(), nbytes,
+                                           self.stream.cuda_stream, ctypes.byref(h)))
+        self._h = h
+        self._keep = {}
+
+    def set_run(self, tol=0.0, steps_per_launch=500, barrier_timeout_s=2.0):
+        _check(self.lib.ddflb_batch_set_run(self._h, float(tol), int(steps_per_launch),
+                                            float(barrier_timeout_s)))
+        return self
+
+    def set_tiles(self, tile_x, tile_y, blocks_per_sm=0):
+        _check(self.lib.ddflb_batch_set_tiles(self._h, tile_x, tile_y, blocks_per_sm))
+        return self
+
+    def tiles(self):
+        v = [ctypes.c_int32() for _ in range(3)]
+        _check(self.lib.ddflb_batch_get_tiles(self._h, *[ctypes.byref(x) for x in v]))
+        return tuple(x.value for x in v)
+
+    def init(self, i, rho, ux, uy, phi, grads=None):
+        t = self.torch
+        dev = lambda a: None if a is None else (
+            t.from_numpy(np.ascontiguousarray(a, np.float32)) if isinstance(a, np.ndarray) else a
+        ).to(device=self.device, dtype=t.float32).contiguous()
+        keep = [dev(a) for a in (rho, ux, uy, phi, grads)]
+        self._keep[i] = keep
+        _check(self.lib.ddflb_batch_init(self._h, int(i), *[_dptr(a) for a in keep]))
+        return self
+
+    def step(self, n=1):
+        _check(self.lib.ddflb_batch_step(self._h, int(n)))
+        return self
+
+    def fields(self, i, names=FIELD_NAMES):
+        c = self.cfgs[i]
+        out = {k: (self.torch.empty((c.ny, c.nx), dtype=self.torch.float32, device=self.device)
+                   if k in names else None) for k in FIELD_NAMES}
+        _check(self.lib.ddflb_batch_fields(self._h, int(i), *[_dptr(out[k]) for k in FIELD_NAMES]))
+        return {k: v for k, v in out.items() if v is not None}
+
+    def stats(self):
+        r = np.zeros(self.n, np.float64)
+        f = np.zeros(self.n, np.int32)
+        s = np.zeros(self.n, np.int64)
+        t = np.zeros(self.n, np.int64)
+        st = self.lib.ddflb_batch_stats(self._h, r.ctypes.data, f.ctypes.data, s.ctypes.data,
+                                        t.ctypes.data)
+        return {"residual": r, "flags": f, "steps_to_tol": s, "state_time": t, "status": st}
+
+    def debug_skip_barrier(self, block):
+        _check(self.lib.ddflb_batch_debug_skip_barrier(self._h, int(block)))
+        return self
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.ddflb_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -1,0 +1,147 @@
+"""Batched persistent step: every instance of a batch must evolve exactly as
+the same lattice run alone through ddflb_step (same per-node arithmetic), and
+the batch bookkeeping (convergence freeze, divergence, bounded barrier waits)
+must behave.  One instance is also checked against the FP64 oracle directly."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O
+from paper_1908_06742_gb300 import build as B
+from paper_1908_06742_gb300 import ddflb as D
+from paper_1908_06742_gb300 import inputs
+from tests.gpu_helpers import np64, rate
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    B.build()
+    D.load()
+
+
+def cfg(nx, ny, bc, nu, check=10, **kw):
+    w = rate(nu)
+    base = dict(nx=nx, ny=ny, bc=bc, omega_f=(0, 0, 0, 1.2, w, w, 1.2, 1.2, 1.2),
+                omega_g=(0, w, w, 1.2, 1.2, 1.2, 1.2, 1.2, 1.2), check_every=check)
+    base.update(kw)
+    return D.Config(**base)
+
+
+def start_fields(c, seed):
+    if c.bc == "periodic":
+        F = inputs.taylor_green(c.nx, 0.02, phi_amp=0.1, ny=c.ny)
+        return (F.rho, F.ux, F.uy, F.phi, F.grads)
+    F = inputs.rest(c.nx, c.ny, phi=0.5 + 0.1 * seed)
+    return (F.rho, F.ux, F.uy, F.phi, None)
+
+
+CFGS = [cfg(40, 30, "cavity", 0.05, u_lid=0.1, phi_lid=1.0, phi_wall=0.0),
+        cfg(64, 64, "periodic", 0.01),
+        cfg(33, 17, "channel", 0.1, u_lid=0.05, phi_lid=2.0, phi_wall=1.0),
+        cfg(130, 70, "cavity", 0.02, u_lid=0.08, phi_lid=1.0, phi_wall=0.2)]
+
+
+def same(a, b):
+    return torch.equal(torch.nan_to_num(a, 9.0), torch.nan_to_num(b, 9.0))
+
+
+@pytest.mark.parametrize("tiles", [(128, 1), (32, 4), (256, 1), (64, 2)])
+def test_batch_equals_single_lattice_runs(tiles):
+    """45 steps in chunks of 7 (graph replays plus a direct remainder launch),
+    every field of every instance bit-identical to the single-lattice path."""
+    steps = 45
+    b = D.Batch(CFGS).set_run(tol=0.0, steps_per_launch=7).set_tiles(*tiles)
+    for i, c in enumerate(CFGS):
+        b.init(i, *start_fields(c, i))
+    b.step(steps)
+    st = b.stats()
+    assert st["status"] == D.OK and not st["flags"].any()
+    assert (st["state_time"] == steps).all()
+    for i, c in enumerate(CFGS):
+        ref = D.Lattice(c).init(*start_fields(c, i)).step(steps).fields()
+        got = b.fields(i)
+        for k in D.FIELD_NAMES:
+            assert same(got[k], ref[k]), (i, k, tiles)
+    # the residual of the last check (t = 40) matches the single path's check
+    for i, c in enumerate(CFGS):
+        r = D.Lattice(c).init(*start_fields(c, i)).step(40).stats()["residual"]
+        assert math.isclose(st["residual"][i], r, rel_tol=1e-12), (i, st["residual"][i], r)
+
+
+def test_batch_instance_matches_oracle():
+    c = CFGS[3]
+    b = D.Batch([c]).set_run(steps_per_launch=50)
+    f = start_fields(c, 3)
+    b.init(0, *f).step(150)
+    got = {k: np64(v) for k, v in b.fields(0).items()}
+    wf, wg = c.rates()
+    p = O.OracleParams(nx=c.nx, ny=c.ny, bc=c.bc, lam_override=wf, lam_phi_override=wg,
+                       u_lid=c.u_lid, phi_lid=c.phi_lid, phi_wall=c.phi_wall)
+    r32 = lambda a: None if a is None else np.asarray(a, np.float32).astype(np.float64)
+    ref = O.OracleLattice(p).init(*[r32(a) for a in f]).step(150).fields()
+    for k in ("ux", "uy", "phi"):
+        err = math.sqrt(np.sum((got[k] - ref[k]) ** 2) / np.sum(ref[k] ** 2))
+        assert err < 1e-5, (k, err)
+
+
+def test_convergence_freezes_instance():
+    """An instance whose residual drops below tol stops; its state is the one
+    the single path reaches one step after the check that froze it."""
+    slow = cfg(48, 48, "cavity", 0.2, check=20, u_lid=0.05)
+    fast = cfg(48, 48, "cavity", 0.2, check=20, u_lid=0.05, phi_lid=0.7)
+    ref = D.Lattice(slow).init(*start_fields(slow, 0))
+    rs = []
+    for _ in range(30):
+        ref.step(20)
+        rs.append(ref.stats()["residual"])
+    tol = rs[10] * 1.0001
+    first = next(k for k, r in enumerate(rs) if r < tol)   # checks at t = 20 (k + 1)
+    t_tol = 20 * (first + 1)
+    b = D.Batch([slow, fast]).set_run(tol=tol, steps_per_launch=40)
+    b.init(0, *start_fields(slow, 0)).init(1, *start_fields(fast, 0))
+    b.step(600)
+    st = b.stats()
+    assert st["flags"][0] == D.INST_CONVERGED and st["steps_to_tol"][0] == t_tol
+    assert st["state_time"][0] == t_tol + 1
+    frozen = b.fields(0)
+    again = D.Lattice(slow).init(*start_fields(slow, 0)).step(t_tol + 1).fields()
+    for k in D.FIELD_NAMES:
+        assert same(frozen[k], again[k]), k
+
+
+def test_divergence_is_isolated():
+    """A NaN in one instance's initial fields flags that instance only."""
+    c0, c1 = cfg(32, 32, "periodic", 0.01), cfg(40, 24, "cavity", 0.05, u_lid=0.1)
+    bad = list(start_fields(c0, 0))
+    bad[0] = bad[0].copy(); bad[0][5, 7] = np.nan
+    b = D.Batch([c0, c1]).set_run(steps_per_launch=25)
+    b.init(0, *bad).init(1, *start_fields(c1, 1)).step(50)
+    st = b.stats()
+    assert st["flags"][0] == D.INST_DIVERGED and st["flags"][1] == 0
+    ref = D.Lattice(c1).init(*start_fields(c1, 1)).step(50).fields()
+    got = b.fields(1)
+    for k in D.FIELD_NAMES:
+        assert same(got[k], ref[k]), k
+
+
+def test_barrier_wait_runs_out_and_reports_timeout():
+    """One CTA never arrives (a flag nothing sets): the others give up after the
+    bounded wait, the launch ends, stats reports ETIMEOUT, and the context stays
+    usable (a new batch runs correctly afterwards)."""
+    c = cfg(64, 64, "periodic", 0.01)
+    b = D.Batch([c]).set_run(steps_per_launch=5, barrier_timeout_s=0.3)
+    b.init(0, *start_fields(c, 0)).debug_skip_barrier(0).step(5)
+    st = b.stats()
+    assert st["status"] == D.ETIMEOUT
+    b.close()
+    torch.cuda.synchronize()
+    b2 = D.Batch([c]).set_run(steps_per_launch=5)
+    b2.init(0, *start_fields(c, 0)).step(10)
+    ref = D.Lattice(c).init(*start_fields(c, 0)).step(10).fields()
+    assert same(b2.fields(0)["omega"], ref["omega"])
