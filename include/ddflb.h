@@ -189,6 +189,17 @@ ddflb_status ddflb_reduce_noalloc(const ddflb_params* p, const void* dev_state,
                                   size_t state_bytes, int32_t mode, double* dev_out,
                                   void* cuda_stream);
 
+/* Autotuner for the step kernel's thread-block shape: times each candidate
+ * (128x1, 256x1, 64x2, 32x4, 64x4, 32x8, 64x1) over trial_steps with CUDA
+ * events and keeps the fastest.  Runs on zeroed populations, so it OVERWRITES
+ * the state and resets the step counter: call it before ddflb_init.
+ * Synchronises the stream. */
+ddflb_status ddflb_autotune(ddflb_ctx* c, int32_t trial_steps, int32_t* block_x,
+                            int32_t* block_y, double* ms_per_step);
+/* Set the step kernel's block shape directly (e.g. from a cached tuning):
+ * block_x a multiple of 32, 32..256 threads in all. */
+ddflb_status ddflb_set_block(ddflb_ctx* c, int32_t block_x, int32_t block_y);
+
 /* Release the handle (host memory only; the workspace stays the caller's). */
 ddflb_status ddflb_destroy(ddflb_ctx* c);
 
@@ -238,6 +249,13 @@ ddflb_status ddflb_batch_fields(ddflb_batch* b, int32_t i, float* rho, float* ux
  * time of the current state.  Synchronises; ETIMEOUT if a barrier wait ran out. */
 ddflb_status ddflb_batch_stats(ddflb_batch* b, double* residual, int32_t* flags,
                                int64_t* steps_to_tol, int64_t* state_time);
+/* Autotuner: times every supported tile shape at full and half residency
+ * (trial_steps per timed launch, CUDA events) and keeps the fastest; returns
+ * the choice and its time per step.  Runs on zeroed populations, so it
+ * OVERWRITES every instance's state and resets the time to 0: call it before
+ * ddflb_batch_init.  Synchronises the stream. */
+ddflb_status ddflb_batch_autotune(ddflb_batch* b, int32_t trial_steps, int32_t* tile_x,
+                                  int32_t* tile_y, int32_t* blocks_per_sm, double* ms_per_step);
 /* Test hook: CTA `block` of the next launch skips its first barrier so that the
  * others' bounded waits run out (-1 disables).  Never faults or hangs. */
 ddflb_status ddflb_batch_debug_skip_barrier(ddflb_batch* b, int32_t block);

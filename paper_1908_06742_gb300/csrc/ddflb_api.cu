@@ -402,6 +402,72 @@ const char* ddflb_last_error(void) { return g_err.c_str(); }
 
 const char* ddflb_version(void) { return "ddflb 0.1 (sm_103a)"; }
 
+// Autotuner for the step kernel's block shape: each candidate runs trial_steps
+// untimed, then trial_steps timed with CUDA events on the context stream; the
+// fastest is kept.  The trials run on zeroed populations (the rest state), so
+// the state is overwritten and the step counter reset: call before ddflb_init.
+ddflb_status ddflb_autotune(ddflb_ctx* c, int32_t trial_steps, int32_t* block_x,
+                            int32_t* block_y, double* ms_per_step) {
+  if (!c || trial_steps < 1) return fail(DDFLB_EINVAL, "NULL handle or trial_steps < 1");
+  static const int shapes[][2] = {{128, 1}, {256, 1}, {64, 2}, {32, 4}, {64, 4}, {32, 8}, {64, 1}};
+  cudaStream_t s = c->L.stream;
+  cudaError_t e = cudaMemsetAsync(c->pops[0], 0, 2 * c->lay.pops_bytes, s);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune clear");
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  dim3 bestb(128, 1, 1);
+  const size_t gofs = 9 * (size_t)c->lay.pitch * c->p.ny * elem_size(c->p.storage);
+  for (const auto& sh : shapes) {
+    c->L.block = dim3(sh[0], sh[1], 1);
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+      if (rep == 1) e = cudaEventRecord(e0, s);
+      for (int i = 0; i < trial_steps && e == cudaSuccess; ++i) {
+        const int src = i & 1;
+        char* fo = (char*)c->pops[src ^ 1];
+        e = launch_step(c->L, c->pops[src], (const char*)c->pops[src] + gofs, fo, fo + gofs,
+                        c->status);
+      }
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) break;
+    if (ms < best) {
+      best = ms;
+      bestb = c->L.block;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune trial");
+  c->L.block = bestb;
+  e = cudaMemsetAsync(c->pops[0], 0, 2 * c->lay.pops_bytes, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune reset");
+  c->cur = 0;
+  c->step = 0;
+  c->snap_step = -1;
+  ddflb_status st = reset_status(c);
+  if (st != DDFLB_OK) return st;
+  if (block_x) *block_x = (int32_t)bestb.x;
+  if (block_y) *block_y = (int32_t)bestb.y;
+  if (ms_per_step) *ms_per_step = best / trial_steps;
+  return DDFLB_OK;
+}
+
+ddflb_status ddflb_set_block(ddflb_ctx* c, int32_t block_x, int32_t block_y) {
+  if (!c) return fail(DDFLB_EINVAL, "NULL handle");
+  if (block_x < 32 || block_y < 1 || block_x % 32 || block_x * block_y > 256 ||
+      block_x * block_y < 32)
+    return fail(DDFLB_EINVAL, "block %d x %d: x a multiple of 32, 32..256 threads", block_x,
+                block_y);
+  c->L.block = dim3(block_x, block_y, 1);
+  return DDFLB_OK;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------

@@ -672,6 +672,80 @@ ddflb_status ddflb_batch_debug_skip_barrier(ddflb_batch* b, int32_t block) {
   return DDFLB_OK;
 }
 
+// Autotuner: times every supported tile shape at full and half residency on
+// the batch itself (CUDA events on the batch stream, one untimed launch then
+// one timed launch of trial_steps each) and keeps the fastest.  The trials run
+// on zeroed populations (the rest state), so this overwrites every instance's
+// state: call it before ddflb_batch_init.
+ddflb_status ddflb_batch_autotune(ddflb_batch* b, int32_t trial_steps, int32_t* tile_x,
+                                  int32_t* tile_y, int32_t* blocks_per_sm, double* ms_per_step) {
+  if (!b || trial_steps < 1) return bfail(DDFLB_EINVAL, "NULL batch or trial_steps < 1");
+  cudaStream_t s = b->stream;
+  cudaError_t e = cudaMemsetAsync(b->ws, 0, b->lay.off_inst, s);
+  if (e != cudaSuccess) return bcuda(e, "autotune clear");
+  std::vector<BatchStatus> st(b->n);
+  for (auto& x : st) {
+    std::memset(&x, 0, sizeof x);
+    x.steps_to_tol = -1;
+    x.residual = NAN;
+  }
+  const double tol = b->tol;
+  b->tol = 0.0;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int bx = 128, by = 1, bb = 0;
+  ddflb_status rs = DDFLB_OK;
+  for (int k = 0; k < kNumShapes && rs == DDFLB_OK; ++k) {
+    for (int half = 0; half < 2 && rs == DDFLB_OK; ++half) {
+      rs = configure(b, kShapes[k][0], kShapes[k][1], 0);
+      if (rs != DDFLB_OK) break;
+      if (half) {
+        if (b->blocks_per_sm < 2) continue;
+        rs = configure(b, kShapes[k][0], kShapes[k][1], b->blocks_per_sm / 2);
+        if (rs != DDFLB_OK) break;
+      }
+      e = launch_chunk(b, s, trial_steps);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+      if (e == cudaSuccess) e = launch_chunk(b, s, trial_steps);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        rs = bcuda(e, "autotune trial");
+        break;
+      }
+      if (ms < best) {
+        best = ms;
+        bx = b->tile_x;
+        by = b->tile_y;
+        bb = b->blocks_per_sm;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->tol = tol;
+  if (rs != DDFLB_OK) return rs;
+  rs = configure(b, bx, by, bb);
+  if (rs != DDFLB_OK) return rs;
+  // back to a clean state at time 0
+  e = cudaMemsetAsync(b->ws, 0, b->lay.off_inst, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_sync, 0, sizeof(BatchSync), s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_status, st.data(), b->n * sizeof(BatchStatus), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return bcuda(e, "autotune reset");
+  b->step = 0;
+  if (tile_x) *tile_x = bx;
+  if (tile_y) *tile_y = by;
+  if (blocks_per_sm) *blocks_per_sm = bb;
+  if (ms_per_step) *ms_per_step = best / trial_steps;
+  return DDFLB_OK;
+}
+
 ddflb_status ddflb_batch_destroy(ddflb_batch* b) {
   if (b && b->graph) cudaGraphExecDestroy(b->graph);
   delete b;

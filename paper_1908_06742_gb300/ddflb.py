@@ -83,6 +83,11 @@ SIGNATURES = {
     "ddflb_batch_fields": (ctypes.c_int, [_VP, ctypes.c_int32] + [_FP] * 8),
     "ddflb_batch_stats": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "ddflb_batch_debug_skip_barrier": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "ddflb_batch_autotune": (ctypes.c_int, [_VP, ctypes.c_int32] +
+                             [ctypes.POINTER(ctypes.c_int32)] * 3 + [ctypes.POINTER(ctypes.c_double)]),
+    "ddflb_autotune": (ctypes.c_int, [_VP, ctypes.c_int32] + [ctypes.POINTER(ctypes.c_int32)] * 2 +
+                       [ctypes.POINTER(ctypes.c_double)]),
+    "ddflb_set_block": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32]),
     "ddflb_batch_destroy": (ctypes.c_int, [_VP]),
     "ddflb_last_error": (ctypes.c_char_p, []),
     "ddflb_version": (ctypes.c_char_p, []),
@@ -276,6 +281,23 @@ class Lattice:
         return {"mass": m.value, "scalar": s.value, "residual": r.value, "step": k.value,
                 "diverged": st == EDIVERGED}
 
+    def autotune(self, trial_steps=10, cache=True):
+        """Pick the step kernel's block shape (cached by workload signature);
+        must run before init (it overwrites the state)."""
+        from . import tuning
+        key = tuning.key("lattice", [self.cfg])
+        hit = tuning.lookup(key) if cache else None
+        if hit:
+            _check(self.lib.ddflb_set_block(self._h, *hit["choice"]))
+            return hit
+        bx, by, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+        _check(self.lib.ddflb_autotune(self._h, int(trial_steps), ctypes.byref(bx),
+                                       ctypes.byref(by), ctypes.byref(ms)))
+        rec = {"choice": [bx.value, by.value], "ms_per_step": ms.value}
+        if cache:
+            tuning.store(key, rec)
+        return rec
+
     def state_bytes(self) -> int:
         return self.lib.ddflb_state_bytes(self._h)
 
@@ -371,6 +393,23 @@ class Batch:
     def debug_skip_barrier(self, block):
         _check(self.lib.ddflb_batch_debug_skip_barrier(self._h, int(block)))
         return self
+
+    def autotune(self, trial_steps=20, cache=True):
+        """Pick tile shape and residency (cached by workload signature); must
+        run before any init (it overwrites every instance's state)."""
+        from . import tuning
+        key = tuning.key("batch", self.cfgs)
+        hit = tuning.lookup(key) if cache else None
+        if hit:
+            return self.set_tiles(*hit["choice"]), hit
+        v = [ctypes.c_int32() for _ in range(3)]
+        ms = ctypes.c_double()
+        _check(self.lib.ddflb_batch_autotune(self._h, int(trial_steps),
+                                             *[ctypes.byref(x) for x in v], ctypes.byref(ms)))
+        rec = {"choice": [x.value for x in v], "ms_per_step": ms.value}
+        if cache:
+            tuning.store(key, rec)
+        return self, rec
 
     def close(self):
         if getattr(self, "_h", None):

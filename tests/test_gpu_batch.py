@@ -130,6 +130,47 @@ def test_divergence_is_isolated():
         assert same(got[k], ref[k]), k
 
 
+def test_c4_batch_sampled_instances_vs_oracle():
+    """The 512-cavity batch (sizes 64..512, Re log-uniform in [100, 3200],
+    Pe = Re, seed 0) after 200 steps, tiles from the autotuner: a size-stratified
+    sample of instances against the oracle (u, phi within 1e-5; S within
+    1e-5 of the largest component's RMS)."""
+    draws = inputs.cavity_batch(512, seed=0)
+    cfgs = []
+    for d in draws:
+        n, U = d["n"], 0.1
+        w = rate(U * n / d["re"])
+        wg = rate(U * n / d["pe"])
+        cfgs.append(D.Config(nx=n, ny=n, bc="cavity", u_lid=U, phi_lid=1.0, phi_wall=0.0,
+                             omega_f=(0, 0, 0, 1.2, w, w, 1.2, 1.2, 1.2),
+                             omega_g=(0, wg, wg, 1.2, 1.2, 1.2, 1.2, 1.2, 1.2), check_every=100))
+    b = D.Batch(cfgs).set_run(tol=0.0, steps_per_launch=100)
+    b.autotune(trial_steps=5, cache=False)
+    for i, c in enumerate(cfgs):
+        F = inputs.rest(c.nx, c.ny, phi=0.0)
+        b.init(i, F.rho, F.ux, F.uy, F.phi)
+    b.step(200)
+    st = b.stats()
+    assert st["status"] == D.OK
+    picks = {}
+    for i, d in enumerate(draws):
+        picks.setdefault(d["n"], i)
+    for n, i in sorted(picks.items()):
+        c = cfgs[i]
+        wf, wg = c.rates()
+        p = O.OracleParams(nx=n, ny=n, bc="cavity", lam_override=wf, lam_phi_override=wg,
+                           u_lid=c.u_lid, phi_lid=1.0, phi_wall=0.0)
+        F = inputs.rest(n, n, phi=0.0)
+        ref = O.OracleLattice(p).init(F.rho, F.ux, F.uy, F.phi).step(200).fields()
+        got = {k: np64(v) for k, v in b.fields(i).items()}
+        e_u = math.sqrt(np.sum((got["ux"] - ref["ux"]) ** 2 + (got["uy"] - ref["uy"]) ** 2) /
+                        np.sum(ref["ux"] ** 2 + ref["uy"] ** 2))
+        e_phi = math.sqrt(np.sum((got["phi"] - ref["phi"]) ** 2) / np.sum(ref["phi"] ** 2))
+        srms = max(math.sqrt(np.mean(ref[k] ** 2)) for k in ("sxx", "sxy", "syy"))
+        e_s = max(math.sqrt(np.mean((got[k] - ref[k]) ** 2)) for k in ("sxx", "sxy", "syy")) / srms
+        assert e_u < 1e-5 and e_phi < 1e-5 and e_s < 1e-5, (n, e_u, e_phi, e_s)
+
+
 def test_barrier_wait_runs_out_and_reports_timeout():
     """One CTA never arrives (a flag nothing sets): the others give up after the
     bounded wait, the launch ends, stats reports ETIMEOUT, and the context stays
