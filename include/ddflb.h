@@ -127,10 +127,12 @@ ddflb_status ddflb_init_host(ddflb_ctx* c, const float* rho, const float* ux, co
 
 /* Advance n >= 0 time steps: one fused pass per step streams f and g (pull),
  * applies the wall rules, collides both lattices in moment space and stores the
- * post-collision deviations.  Every check_every steps a reduction records the
- * mass, scalar and velocity residual r = |u(t)-u(t-1)|_2 / |u(t)|_2 (FP64
- * sums) in the device status block; once a sum is non-finite further steps are
- * skipped and the next ddflb_stats returns EDIVERGED. */
+ * post-collision deviations.  At every multiple K of check_every a reduction
+ * records the mass, scalar and the velocity residual
+ * r = |u(t) - u(t-K)|_2 / (K |u(t)|_2) (FP64 sums; the mean relative change
+ * per step over the interval, which stays above the FP32 rounding jitter of a
+ * one-step difference) in the device status block; once a sum is non-finite
+ * further steps are skipped and the next ddflb_stats returns EDIVERGED. */
 ddflb_status ddflb_step(ddflb_ctx* c, int64_t n);
 
 /* Local kinematics of the current state (Sec. 4): density, velocity, scalar,
@@ -211,7 +213,7 @@ ddflb_status ddflb_destroy(ddflb_ctx* c);
  * bounded in time (a wait that runs out ends the launch; *_stats then returns
  * ETIMEOUT).  A chunk launch is captured once as a CUDA graph and replayed.
  * All instances share storage precision and check_every.  Every check_every
- * steps each instance's residual r = |u(t)-u(t-1)|/|u(t)| is reduced in a
+ * steps each instance's residual r = |u(t)-u(t-K)|/(K |u(t)|) is reduced in a
  * fixed order; an instance whose r falls below the tolerance (converged) or
  * whose sums are not finite (diverged) is frozen from then on. */
 #define DDFLB_INST_CONVERGED 1

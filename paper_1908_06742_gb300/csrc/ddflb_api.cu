@@ -195,16 +195,15 @@ ddflb_status reduce(ddflb_ctx* c, int mode) {
   return DDFLB_OK;
 }
 
-// residual bookkeeping around step s (state time): a snapshot of u at
-// s = K*j - 1 and a check against it at s = K*j.
+// Residual bookkeeping at state time s: at every multiple of K the velocity is
+// compared with the snapshot taken K steps earlier, then becomes the next
+// snapshot (one pass).  The reported residual is |u(s) - u(s-K)| / (K |u(s)|).
 ddflb_status checks_at(ddflb_ctx* c) {
   const int K = c->p.check_every;
   if (K <= 0) return DDFLB_OK;
   const int64_t s = c->step;
-  int mode = 0;
-  if (s > 0 && s % K == 0 && c->snap_step == s - 1) mode |= 1;
-  if (s % K == K - 1) mode |= 2;
-  if (mode == 0) return DDFLB_OK;
+  if (s % K != 0) return DDFLB_OK;
+  const int mode = (s > 0 && c->snap_step == s - K ? 1 : 0) | 2;
   return reduce(c, mode);
 }
 
@@ -361,7 +360,7 @@ ddflb_status ddflb_stats(ddflb_ctx* c, double* mass, double* scalar, double* res
   const double cells = (double)c->p.nx * c->p.ny;
   if (mass) *mass = cells * c->p.rho0 + h.mass_dev;
   if (scalar) *scalar = cells * c->p.phi0 + h.scalar_dev;
-  if (residual) *residual = h.has_residual ? h.residual : NAN;
+  if (residual) *residual = h.has_residual ? h.residual / c->p.check_every : NAN;
   if (step) *step = c->step;
   if (h.diverged) return fail(DDFLB_EDIVERGED, "non-finite mass/scalar sum by step %lld",
                               (long long)c->step);

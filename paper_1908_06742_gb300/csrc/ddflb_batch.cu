@@ -49,6 +49,7 @@ struct BatchStatus {
   double mass_dev;
   int64_t steps_to_tol;  // state time at which the residual first fell below tol (-1: not yet)
   int64_t state_time;    // state time of the instance's current state when frozen
+  long long init_time;   // state time at which the instance was (re)initialised
   int32_t flags;         // DDFLB_INST_CONVERGED | DDFLB_INST_DIVERGED
   int32_t pad;
 };
@@ -173,6 +174,7 @@ __global__ void __launch_bounds__(256) k_batch(BatchArgs A) {
   __shared__ BatchInst sI;
   __shared__ double sh[8];
   __shared__ int sActive;
+  __shared__ long long sInit;
   const int64_t t0 = A.sync->step;
   const LbParams& sP = sI.P;
   // each CTA owns a contiguous range of tiles: instance parameters are staged
@@ -183,8 +185,10 @@ __global__ void __launch_bounds__(256) k_batch(BatchArgs A) {
   for (int s = 0; s < A.nsteps; ++s) {
     const int64_t t = t0 + s;
     const int src = (int)(t & 1);
-    const bool check = A.check_every > 0 && t > 0 && t % A.check_every == 0;
-    const bool snap = A.check_every > 0 && t % A.check_every == A.check_every - 1;
+    // at every multiple of K: compare u with the snapshot from K steps earlier
+    // (instances initialised at least K steps ago), then take the next snapshot
+    const bool snap = A.check_every > 0 && t % A.check_every == 0;
+    const bool check_t = snap && t > 0;
     for (int tile = tb; tile < te; ++tile) {
       const int4 T = A.tiles[tile];
       if (T.x != cur) {
@@ -192,11 +196,15 @@ __global__ void __launch_bounds__(256) k_batch(BatchArgs A) {
         const int* srcw = (const int*)(A.inst + T.x);
         int* dstw = (int*)&sI;
         for (int w = threadIdx.x; w < (int)(sizeof(BatchInst) / 4); w += blockDim.x) dstw[w] = srcw[w];
-        if (threadIdx.x == 0) sActive = __ldcg(&A.ist[T.x].flags) == 0;
+        if (threadIdx.x == 0) {
+          sActive = __ldcg(&A.ist[T.x].flags) == 0;
+          sInit = __ldcg(&A.ist[T.x].init_time);
+        }
         cur = T.x;
         __syncthreads();
       }
       if (!sActive) continue;
+      const bool check = check_t && t - A.check_every >= sInit;
       const int x = T.y + threadIdx.x % A.tile_x, y = T.z + threadIdx.x / A.tile_x;
       double acc[3] = {0.0, 0.0, 0.0};
       if (x < sP.nx && y < sP.ny) {
@@ -213,11 +221,11 @@ __global__ void __launch_bounds__(256) k_batch(BatchArgs A) {
         }
       }
     }
-    if (check) {
+    if (check_t) {
       if (!grid_barrier(A.sync, A.timeout_ns)) return;
       // per-instance fixed-order reduction of the tile sums
       for (int i = blockIdx.x; i < A.ninst; i += gridDim.x) {
-        if (__ldcg(&A.ist[i].flags) != 0) continue;
+        if (__ldcg(&A.ist[i].flags) != 0 || t - A.check_every < __ldcg(&A.ist[i].init_time)) continue;
         const int b = A.inst[i].tile_begin, e = A.inst[i].tile_end;
         double v[3];
         for (int k = 0; k < 3; ++k) {
@@ -229,7 +237,7 @@ __global__ void __launch_bounds__(256) k_batch(BatchArgs A) {
           BatchStatus& st = A.ist[i];
           st.u2 = v[0];
           st.mass_dev = v[2];
-          st.residual = v[0] > 0.0 ? sqrt(v[1] / v[0]) : 0.0;
+          st.residual = v[0] > 0.0 ? sqrt(v[1] / v[0]) / A.check_every : 0.0;
           if (!isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2])) {
             st.flags = DDFLB_INST_DIVERGED;
             st.state_time = t + 1;
@@ -600,6 +608,7 @@ ddflb_status ddflb_batch_init(ddflb_batch* b, int32_t i, const float* rho, const
   std::memset(&s, 0, sizeof s);
   s.steps_to_tol = -1;
   s.residual = NAN;
+  s.init_time = b->step;
   e = cudaMemcpyAsync(b->d_status + i, &s, sizeof s, cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   return e == cudaSuccess ? DDFLB_OK : bcuda(e, "batch init status");
