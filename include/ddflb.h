@@ -263,6 +263,68 @@ ddflb_status ddflb_batch_autotune(ddflb_batch* b, int32_t trial_steps, int32_t* 
 ddflb_status ddflb_batch_debug_skip_barrier(ddflb_batch* b, int32_t block);
 ddflb_status ddflb_batch_destroy(ddflb_batch* b);
 
+/* ---------------------------------------------------------------------------
+ * Warm-start surrogate network kernels.  The paper has no network; these
+ * serve the learned warm start (a small U-Net that predicts steady cavity
+ * fields from the flow parameters; its output only initialises the
+ * populations, the method then runs to the residual tolerance as usual).
+ * Tensors: BF16 (__nv_bfloat16 bits) or FP32 device arrays, activations NHWC
+ * with a channel stride cs (so a concatenation is two writers of one buffer).
+ * All calls are asynchronous on `stream`; errors: EINVAL (shapes, alignment),
+ * ECUDA (launch). */
+
+/* C = act(A . B^T + bias) on tensor cores, FP32 accumulation.  A [M][K]
+ * (row stride lda), B [N][K] (ldb): BF16, K-contiguous, 16-byte aligned, K,
+ * lda, ldb multiples of 8.  Outputs: Cf FP32 [M][ldc] and/or Cb BF16
+ * [M][ldcb] (either may be NULL); bias FP32 [N] or NULL; act 0 = none,
+ * 1 = leaky ReLU (slope 0.02); accumulate: Cf += result.  splits > 1 splits
+ * the K range over that many CTA slices writing to `partial` (FP32, at least
+ * splits*M*N, caller-owned), summed in a fixed order afterwards (Cf only). */
+ddflb_status ddflb_nn_gemm(const void* A, const void* B, int32_t M, int32_t N, int32_t K,
+                           int32_t lda, int32_t ldb, float* Cf, int32_t ldc, void* Cb,
+                           int32_t ldcb, const float* bias, int32_t act, int32_t accumulate,
+                           int32_t splits, float* partial, void* stream);
+/* 3x3 patches of X (BF16 NHWC [B][H][W][C], stride cs, zero padding):
+ * col [B*H*W][9*C] (tap-major then channel), or transposed [9*C][B*H*W]. */
+ddflb_status ddflb_nn_im2col(const void* X, int32_t B, int32_t H, int32_t W, int32_t C,
+                             int32_t cs, void* col, int32_t transposed, void* stream);
+/* Adjoint of im2col: dX[b][h][w][c] (FP32, stride cs) = sum of the 9 patch
+ * entries dcol [B*H*W][9*C] (FP32) that read (h, w). */
+ddflb_status ddflb_nn_col2im(const float* dcol, int32_t B, int32_t H, int32_t W, int32_t C,
+                             float* dX, int32_t cs, void* stream);
+/* dst [N][M] = src [M][N] (BF16, src row stride lds). */
+ddflb_status ddflb_nn_transpose(const void* src, int32_t M, int32_t N, int32_t lds, void* dst,
+                                void* stream);
+/* 2x2 average pooling (BF16) and its adjoint (FP32, optionally accumulating). */
+ddflb_status ddflb_nn_pool(const void* X, int32_t B, int32_t H, int32_t W, int32_t C, int32_t csx,
+                           void* Y, int32_t csy, void* stream);
+ddflb_status ddflb_nn_pool_bwd(const float* dY, int32_t B, int32_t H, int32_t W, int32_t C,
+                               int32_t csy, float* dX, int32_t csx, int32_t accumulate,
+                               void* stream);
+/* Nearest 2x upsampling (BF16, input H x W) and its adjoint (FP32). */
+ddflb_status ddflb_nn_upsample(const void* X, int32_t B, int32_t H, int32_t W, int32_t C,
+                               int32_t csx, void* Y, int32_t csy, void* stream);
+ddflb_status ddflb_nn_upsample_bwd(const float* dY, int32_t B, int32_t H, int32_t W, int32_t C,
+                                   int32_t csy, float* dX, int32_t csx, void* stream);
+/* g *= act'(.) read from the activation output y (BF16); optional BF16 copy gb. */
+ddflb_status ddflb_nn_act_bwd(float* g, const void* y, int64_t rows, int32_t C, int32_t csg,
+                              int32_t csy, int32_t act, void* gb, int32_t csb, void* stream);
+/* db[c] = sum over rows of g[r][c] (FP32). */
+ddflb_status ddflb_nn_bias_grad(const float* g, int64_t rows, int32_t C, int32_t cs, float* db,
+                                void* stream);
+/* Mean squared error of n FP32 values into *dev_loss (FP64), optional gradient
+ * 2 (pred - target) / n; dev_partial: 256 doubles of caller scratch. */
+ddflb_status ddflb_nn_mse(const float* pred, const float* target, int64_t n, float* grad,
+                          double* dev_partial, double* dev_loss, void* stream);
+/* Adam step t >= 1 on FP32 weights w with moments m, v (decoupled weight
+ * decay wd); refreshes the BF16 copy wb if not NULL. */
+ddflb_status ddflb_nn_adam(float* w, const float* g, float* m, float* v, void* wb, int64_t n,
+                           float lr, float beta1, float beta2, float eps, int64_t t, float wd,
+                           void* stream);
+/* y (BF16, stride csy) = x (FP32, stride csx), rows x C. */
+ddflb_status ddflb_nn_cast_bf16(const float* x, int64_t rows, int32_t C, int32_t csx, void* y,
+                                int32_t csy, void* stream);
+
 /* Message of the last error on the calling thread ("" if none). */
 const char* ddflb_last_error(void);
 

@@ -1,0 +1,565 @@
+// Kernels of the warm-start surrogate network (a small U-Net): BF16 tensor-core
+// GEMM with FP32 accumulation and a fused bias + activation epilogue, plus the
+// data-movement kernels that turn 3x3 convolutions into GEMMs (im2col in two
+// layouts, col2im), pooling, upsampling, the activation derivative, bias
+// gradients, the MSE loss and Adam.
+//
+// Tensors are NHWC with an explicit channel stride ("cs"), so a concatenation
+// is two producers writing disjoint channel slices of one buffer.
+//
+// GEMM convention: C[M][N] = A[M][K] . B[N][K]^T (both operands K-contiguous,
+// row-major), i.e. a convolution forward pass is C = im2col(X) . W^T with
+// W[Cout][3][3][Cin].
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+
+#include "../../include/ddflb.h"
+#include "ddflb_internal.h"
+
+namespace ddflb {
+namespace nn {
+
+typedef __nv_bfloat16 bf16;
+
+__device__ __forceinline__ float act_fwd(float z, int act) {
+  return act == 1 ? (z > 0.f ? z : 0.02f * z) : z;  // 1: leaky ReLU, slope 0.02
+}
+
+// ------------------------------------------------------------------ GEMM
+// 128 x 128 CTA tile, K step 32, 8 warps (2 along M x 4 along N), each warp a
+// 64 x 32 tile of m16n8k16 MMAs; operands staged in padded shared memory by
+// cp.async with a two-stage pipeline.
+constexpr int BM = 128, BN = 128, BK = 32, LDS = BK + 8;  // +8 bf16: conflict-free ldmatrix
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool pred) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  const int n = pred ? 16 : 0;  // src-size 0: zero fill
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(n));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n"); }
+
+__device__ __forceinline__ void ldsm_x4(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3,
+                                        const void* p) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(s));
+}
+
+__device__ __forceinline__ void mma16816(float c[4], const unsigned a[4], const unsigned b[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+struct GemmArgs {
+  const bf16* A;
+  const bf16* B;
+  int M, N, K, lda, ldb;
+  float* Cf;   // optional FP32 output [M][ldc]
+  bf16* Cb;    // optional BF16 output [M][ldcb]
+  int ldc, ldcb;
+  const float* bias;  // optional [N]
+  int act;
+  int accumulate;  // Cf += result (FP32 only)
+  int kchunk;      // K range per blockIdx.z (split-K); == K when not split
+  float* partial;  // split-K: slice z written to partial + z*M*N (row-major [M][N])
+};
+
+__global__ void __launch_bounds__(256) k_gemm(GemmArgs g) {
+  __shared__ __align__(16) bf16 sA[2][BM * LDS];
+  __shared__ __align__(16) bf16 sB[2][BN * LDS];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int wm = (warp >> 2) * 64, wn = (warp & 3) * 32;
+  float acc[4][4][4] = {};
+  const int kbeg = blockIdx.z * g.kchunk, kend = min(g.K, kbeg + g.kchunk);
+
+  // each thread moves 2 x 16 B of A and of B per K step (128 rows x 4 chunks)
+  auto load = [&](int stage, int k0) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int idx = tid + r * 256, row = idx >> 2, ch = (idx & 3) * 8;
+      const int gm = m0 + row, gk = k0 + ch;
+      const bool pa = gm < g.M && gk < kend;
+      cp_async16(&sA[stage][row * LDS + ch], pa ? g.A + (size_t)gm * g.lda + gk : g.A, pa);
+      const int gn = n0 + row;
+      const bool pb = gn < g.N && gk < kend;
+      cp_async16(&sB[stage][row * LDS + ch], pb ? g.B + (size_t)gn * g.ldb + gk : g.B, pb);
+    }
+    cp_async_commit();
+  };
+
+  const int nk = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;
+  if (nk > 0) load(0, kbeg);
+  for (int kt = 0; kt < nk; ++kt) {
+    const int st = kt & 1;
+    cp_async_wait0();
+    __syncthreads();
+    if (kt + 1 < nk) load(st ^ 1, kbeg + (kt + 1) * BK);
+#pragma unroll
+    for (int kk = 0; kk < BK; kk += 16) {
+      unsigned af[4][4], bfr[4][2];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int row = wm + i * 16 + (lane & 15), col = kk + (lane >> 4) * 8;
+        ldsm_x4(af[i][0], af[i][1], af[i][2], af[i][3], &sA[st][row * LDS + col]);
+      }
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        // two n8 tiles per ldmatrix.x4: rows n = wn + j*16 + (lane & 7) + ((lane >> 4) << 3)
+        const int row = wn + j * 16 + (lane & 7) + ((lane >> 4) << 3);
+        const int col = kk + ((lane >> 3) & 1) * 8;
+        unsigned r0, r1, r2, r3;
+        ldsm_x4(r0, r1, r2, r3, &sB[st][row * LDS + col]);
+        bfr[2 * j][0] = r0;
+        bfr[2 * j][1] = r1;
+        bfr[2 * j + 1][0] = r2;
+        bfr[2 * j + 1][1] = r3;
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) mma16816(acc[i][j], af[i], bfr[j]);
+    }
+    __syncthreads();
+  }
+  // epilogue: c0,c1 at (lane/4, 2(lane%4) + {0,1}); c2,c3 eight rows below
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int r = m0 + wm + i * 16 + (lane >> 2) + h * 8;
+        const int c = n0 + wn + j * 8 + (lane & 3) * 2;
+        if (r >= g.M) continue;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          if (c + e >= g.N) continue;
+          float v = acc[i][j][2 * h + e];
+          if (g.partial) {
+            g.partial[((size_t)blockIdx.z * g.M + r) * g.N + c + e] = v;
+            continue;
+          }
+          if (g.bias) v += g.bias[c + e];
+          v = act_fwd(v, g.act);
+          if (g.Cf) {
+            float* p = g.Cf + (size_t)r * g.ldc + c + e;
+            *p = g.accumulate ? *p + v : v;
+          }
+          if (g.Cb) g.Cb[(size_t)r * g.ldcb + c + e] = __float2bfloat16_rn(v);
+        }
+      }
+}
+
+// split-K: C = sum over slices z (fixed order) of partial[z]; then bias, act
+__global__ void k_splitk_reduce(const float* __restrict__ partial, int splits, int M, int N,
+                                float* __restrict__ Cf, int ldc, const float* __restrict__ bias,
+                                int act, int accumulate) {
+  const int64_t total = (int64_t)M * N;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float v = 0.f;
+    for (int z = 0; z < splits; ++z) v += partial[(int64_t)z * total + i];
+    const int r = (int)(i / N), c = (int)(i % N);
+    if (bias) v += bias[c];
+    v = act_fwd(v, act);
+    float* p = Cf + (size_t)r * ldc + c;
+    *p = accumulate ? *p + v : v;
+  }
+}
+
+// ------------------------------------------------------------------ conv helpers
+// im2col: col[p][(kh*3 + kw)*C + c] = X[b][h + kh - 1][w + kw - 1][c] (zero outside)
+__global__ void k_im2col(const bf16* __restrict__ X, int B, int H, int W, int C, int cs,
+                         bf16* __restrict__ col) {
+  const int64_t total = (int64_t)B * H * W * 9 * C;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    const int64_t r = i / C;
+    const int tap = (int)(r % 9);
+    const int64_t p = r / 9;
+    const int w = (int)(p % W), h = (int)((p / W) % H), b = (int)(p / ((int64_t)W * H));
+    const int hh = h + tap / 3 - 1, ww = w + tap % 3 - 1;
+    bf16 v = __float2bfloat16_rn(0.f);
+    if (hh >= 0 && hh < H && ww >= 0 && ww < W) v = X[(((int64_t)b * H + hh) * W + ww) * cs + c];
+    col[i] = v;
+  }
+}
+
+// transposed im2col: colT[(kh*3 + kw)*C + c][p] (pixels contiguous)
+__global__ void k_im2col_t(const bf16* __restrict__ X, int B, int H, int W, int C, int cs,
+                           bf16* __restrict__ colT) {
+  const int64_t P = (int64_t)B * H * W, total = P * 9 * C;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = i % P;
+    const int64_t k = i / P;
+    const int c = (int)(k % C), tap = (int)(k / C);
+    const int w = (int)(p % W), h = (int)((p / W) % H), b = (int)(p / ((int64_t)W * H));
+    const int hh = h + tap / 3 - 1, ww = w + tap % 3 - 1;
+    bf16 v = __float2bfloat16_rn(0.f);
+    if (hh >= 0 && hh < H && ww >= 0 && ww < W) v = X[(((int64_t)b * H + hh) * W + ww) * cs + c];
+    colT[i] = v;
+  }
+}
+
+// col2im: dX[b][h][w][c] = sum over taps of dcol[pixel that reads (h, w)][tap][c]
+__global__ void k_col2im(const float* __restrict__ dcol, int B, int H, int W, int C,
+                         float* __restrict__ dX, int cs) {
+  const int64_t total = (int64_t)B * H * W * C;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    const int64_t p = i / C;
+    const int w = (int)(p % W), h = (int)((p / W) % H), b = (int)(p / ((int64_t)W * H));
+    float s = 0.f;
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int ho = h - (tap / 3 - 1), wo = w - (tap % 3 - 1);  // output pixel reading (h, w)
+      if (ho >= 0 && ho < H && wo >= 0 && wo < W)
+        s += dcol[((((int64_t)b * H + ho) * W + wo) * 9 + tap) * C + c];
+    }
+    dX[p * cs + c] = s;
+  }
+}
+
+// dst[n][m] = src[m][n] (BF16, src row stride lds)
+__global__ void k_transpose(const bf16* __restrict__ src, int M, int N, int lds,
+                            bf16* __restrict__ dst) {
+  __shared__ bf16 t[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const int m = by + j, n = bx + threadIdx.x;
+    if (m < M && n < N) t[j][threadIdx.x] = src[(size_t)m * lds + n];
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const int n = bx + j, m = by + threadIdx.x;
+    if (m < M && n < N) dst[(size_t)n * M + m] = t[threadIdx.x][j];
+  }
+}
+
+// 2x2 average pool (fwd) / its adjoint (bwd), nearest 2x upsample (fwd) / adjoint (bwd)
+__global__ void k_pool(const bf16* __restrict__ X, int B, int H, int W, int C, int csx,
+                       bf16* __restrict__ Y, int csy) {
+  const int Ho = H / 2, Wo = W / 2;
+  const int64_t total = (int64_t)B * Ho * Wo * C;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    const int64_t p = i / C;
+    const int w = (int)(p % Wo), h = (int)((p / Wo) % Ho), b = (int)(p / ((int64_t)Wo * Ho));
+    float s = 0.f;
+    for (int dy = 0; dy < 2; ++dy)
+      for (int dx = 0; dx < 2; ++dx)
+        s += __bfloat162float(X[(((int64_t)b * H + 2 * h + dy) * W + 2 * w + dx) * csx + c]);
+    Y[p * csy + c] = __float2bfloat16_rn(0.25f * s);
+  }
+}
+
+__global__ void k_pool_bwd(const float* __restrict__ dY, int B, int H, int W, int C, int csy,
+                           float* __restrict__ dX, int csx, int accumulate) {
+  const int64_t total = (int64_t)B * H * W * C;  // H, W of the input (fine) grid
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    const int64_t p = i / C;
+    const int w = (int)(p % W), h = (int)((p / W) % H), b = (int)(p / ((int64_t)W * H));
+    const float v = 0.25f * dY[(((int64_t)b * (H / 2) + h / 2) * (W / 2) + w / 2) * csy + c];
+    float* d = dX + p * csx + c;
+    *d = accumulate ? *d + v : v;
+  }
+}
+
+__global__ void k_upsample(const bf16* __restrict__ X, int B, int H, int W, int C, int csx,
+                           bf16* __restrict__ Y, int csy) {
+  const int64_t total = (int64_t)B * 2 * H * 2 * W * C;  // output grid 2H x 2W
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    const int64_t p = i / C;
+    const int w = (int)(p % (2 * W)), h = (int)((p / (2 * W)) % (2 * H));
+    const int b = (int)(p / ((int64_t)4 * W * H));
+    Y[p * csy + c] = X[(((int64_t)b * H + h / 2) * W + w / 2) * csx + c];
+  }
+}
+
+__global__ void k_upsample_bwd(const float* __restrict__ dY, int B, int H, int W, int C, int csy,
+                               float* __restrict__ dX, int csx) {
+  const int64_t total = (int64_t)B * H * W * C;  // coarse grid
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    const int64_t p = i / C;
+    const int w = (int)(p % W), h = (int)((p / W) % H), b = (int)(p / ((int64_t)W * H));
+    float s = 0.f;
+    for (int dy = 0; dy < 2; ++dy)
+      for (int dx = 0; dx < 2; ++dx)
+        s += dY[(((int64_t)b * 2 * H + 2 * h + dy) * 2 * W + 2 * w + dx) * csy + c];
+    dX[p * csx + c] = s;
+  }
+}
+
+// gradient through the activation: g *= f'(z), with f' read from the output y
+// (leaky ReLU: 1 where y > 0, else the slope); writes FP32 and a BF16 copy
+__global__ void k_act_bwd(float* __restrict__ g, const bf16* __restrict__ y, int64_t rows, int C,
+                          int csg, int csy, int act, bf16* __restrict__ gb, int csb) {
+  const int64_t total = rows * C;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    const int64_t r = i / C;
+    float v = g[r * csg + c];
+    if (act == 1 && !(__bfloat162float(y[r * csy + c]) > 0.f)) v *= 0.02f;
+    g[r * csg + c] = v;
+    if (gb) gb[r * csb + c] = __float2bfloat16_rn(v);
+  }
+}
+
+// db[c] = sum over rows of g[r][c] (fixed order per channel)
+__global__ void k_bias_grad(const float* __restrict__ g, int64_t rows, int C, int cs,
+                            float* __restrict__ db) {
+  const int c = blockIdx.x;
+  __shared__ float sh[256];
+  float s = 0.f;
+  for (int64_t r = threadIdx.x; r < rows; r += blockDim.x) s += g[r * cs + c];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) db[c] = sh[0];
+}
+
+// loss = mean((pred - target)^2) over rows x C; grad = 2 (pred - target) / count
+__global__ void k_mse(const float* __restrict__ pred, const float* __restrict__ target,
+                      int64_t n, float* __restrict__ grad, double* __restrict__ partial) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float d = pred[i] - target[i];
+    s += (double)d * d;
+    if (grad) grad[i] = 2.0f * d / (float)n;
+  }
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+__global__ void k_sum(const double* __restrict__ partial, int n, double scale,
+                      double* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0;
+  for (int i = 0; i < n; ++i) s += partial[i];
+  *out = s * scale;
+}
+
+// Adam on FP32 master weights, refreshes the BF16 copy used by the GEMMs
+__global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, bf16* __restrict__ wb, int64_t n, float lr,
+                       float b1, float b2, float eps, float c1, float c2, float wd) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = g[i] + wd * w[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    w[i] = wi;
+    if (wb) wb[i] = __float2bfloat16_rn(wi);
+  }
+}
+
+__global__ void k_cast_bf16(const float* __restrict__ x, int64_t rows, int C, int csx,
+                            bf16* __restrict__ y, int csy) {
+  const int64_t total = rows * C;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    const int64_t r = i / C;
+    y[r * csy + c] = __float2bfloat16_rn(x[r * csx + c]);
+  }
+}
+
+int grid_for(int64_t n) {
+  const int64_t g = (n + 255) / 256;
+  return (int)(g < 152 * 32 ? (g < 1 ? 1 : g) : 152 * 32);
+}
+
+}  // namespace nn
+}  // namespace ddflb
+
+using namespace ddflb::nn;
+
+namespace {
+ddflb_status launched(const char* what) {
+  const cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) return DDFLB_OK;
+  char buf[256];
+  snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+  ddflb::set_error(buf);
+  return DDFLB_ECUDA;
+}
+ddflb_status bad(const char* msg) {
+  ddflb::set_error(msg);
+  return DDFLB_EINVAL;
+}
+}  // namespace
+
+extern "C" {
+
+ddflb_status ddflb_nn_gemm(const void* A, const void* B, int32_t M, int32_t N, int32_t K,
+                           int32_t lda, int32_t ldb, float* Cf, int32_t ldc, void* Cb,
+                           int32_t ldcb, const float* bias, int32_t act, int32_t accumulate,
+                           int32_t splits, float* partial, void* stream) {
+  if (!A || !B || M <= 0 || N <= 0 || K <= 0 || (!Cf && !Cb)) return bad("gemm: bad arguments");
+  if (K % 8 || lda % 8 || ldb % 8 || ((uintptr_t)A % 16) || ((uintptr_t)B % 16))
+    return bad("gemm: K, lda, ldb must be multiples of 8 and A, B 16-byte aligned");
+  if (lda < K || ldb < K || (Cf && ldc < N) || (Cb && ldcb < N)) return bad("gemm: leading dims");
+  if (act < 0 || act > 1) return bad("gemm: act must be 0 (none) or 1 (leaky ReLU)");
+  if (splits < 1) return bad("gemm: splits < 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (splits == 1) {
+    GemmArgs g{(const bf16*)A, (const bf16*)B, M, N, K, lda, ldb, Cf, (bf16*)Cb, ldc, ldcb,
+               bias, act, accumulate, K, nullptr};
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+    k_gemm<<<grid, 256, 0, s>>>(g);
+    return launched("gemm");
+  }
+  if (!Cf || Cb || !partial) return bad("gemm: split-K needs Cf and partial (and no Cb)");
+  int kchunk = (K + splits - 1) / splits;
+  kchunk = (kchunk + BK - 1) / BK * BK;
+  const int z = (K + kchunk - 1) / kchunk;  // <= splits slices of the partial buffer
+  GemmArgs g{(const bf16*)A, (const bf16*)B, M, N, K, lda, ldb, nullptr, nullptr, 0, 0, nullptr,
+             0, 0, kchunk, partial};
+  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, z);
+  k_gemm<<<grid, 256, 0, s>>>(g);
+  k_splitk_reduce<<<grid_for((int64_t)M * N), 256, 0, s>>>(partial, z, M, N, Cf, ldc, bias, act,
+                                                           accumulate);
+  return launched("gemm split-K");
+}
+
+ddflb_status ddflb_nn_im2col(const void* X, int32_t B, int32_t H, int32_t W, int32_t C,
+                             int32_t cs, void* col, int32_t transposed, void* stream) {
+  if (!X || !col || B <= 0 || H <= 0 || W <= 0 || C <= 0 || cs < C) return bad("im2col: bad args");
+  const int64_t n = (int64_t)B * H * W * 9 * C;
+  if (transposed)
+    k_im2col_t<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>((const bf16*)X, B, H, W, C, cs,
+                                                              (bf16*)col);
+  else
+    k_im2col<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>((const bf16*)X, B, H, W, C, cs,
+                                                            (bf16*)col);
+  return launched("im2col");
+}
+
+ddflb_status ddflb_nn_col2im(const float* dcol, int32_t B, int32_t H, int32_t W, int32_t C,
+                             float* dX, int32_t cs, void* stream) {
+  if (!dcol || !dX || B <= 0 || H <= 0 || W <= 0 || C <= 0 || cs < C) return bad("col2im: bad args");
+  const int64_t n = (int64_t)B * H * W * C;
+  k_col2im<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(dcol, B, H, W, C, dX, cs);
+  return launched("col2im");
+}
+
+ddflb_status ddflb_nn_transpose(const void* src, int32_t M, int32_t N, int32_t lds, void* dst,
+                                void* stream) {
+  if (!src || !dst || M <= 0 || N <= 0 || lds < N) return bad("transpose: bad args");
+  dim3 grid((N + 31) / 32, (M + 31) / 32), block(32, 8);
+  k_transpose<<<grid, block, 0, (cudaStream_t)stream>>>((const bf16*)src, M, N, lds, (bf16*)dst);
+  return launched("transpose");
+}
+
+ddflb_status ddflb_nn_pool(const void* X, int32_t B, int32_t H, int32_t W, int32_t C, int32_t csx,
+                           void* Y, int32_t csy, void* stream) {
+  if (!X || !Y || H % 2 || W % 2 || C <= 0) return bad("pool: bad args");
+  const int64_t n = (int64_t)B * (H / 2) * (W / 2) * C;
+  k_pool<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>((const bf16*)X, B, H, W, C, csx,
+                                                        (bf16*)Y, csy);
+  return launched("pool");
+}
+
+ddflb_status ddflb_nn_pool_bwd(const float* dY, int32_t B, int32_t H, int32_t W, int32_t C,
+                               int32_t csy, float* dX, int32_t csx, int32_t accumulate,
+                               void* stream) {
+  if (!dY || !dX || H % 2 || W % 2 || C <= 0) return bad("pool_bwd: bad args");
+  const int64_t n = (int64_t)B * H * W * C;
+  k_pool_bwd<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(dY, B, H, W, C, csy, dX, csx,
+                                                            accumulate);
+  return launched("pool_bwd");
+}
+
+ddflb_status ddflb_nn_upsample(const void* X, int32_t B, int32_t H, int32_t W, int32_t C,
+                               int32_t csx, void* Y, int32_t csy, void* stream) {
+  if (!X || !Y || C <= 0) return bad("upsample: bad args");
+  const int64_t n = (int64_t)B * 4 * H * W * C;
+  k_upsample<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>((const bf16*)X, B, H, W, C, csx,
+                                                            (bf16*)Y, csy);
+  return launched("upsample");
+}
+
+ddflb_status ddflb_nn_upsample_bwd(const float* dY, int32_t B, int32_t H, int32_t W, int32_t C,
+                                   int32_t csy, float* dX, int32_t csx, void* stream) {
+  if (!dY || !dX || C <= 0) return bad("upsample_bwd: bad args");
+  const int64_t n = (int64_t)B * H * W * C;
+  k_upsample_bwd<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(dY, B, H, W, C, csy, dX, csx);
+  return launched("upsample_bwd");
+}
+
+ddflb_status ddflb_nn_act_bwd(float* g, const void* y, int64_t rows, int32_t C, int32_t csg,
+                              int32_t csy, int32_t act, void* gb, int32_t csb, void* stream) {
+  if (!g || !y || rows <= 0 || C <= 0) return bad("act_bwd: bad args");
+  k_act_bwd<<<grid_for(rows * C), 256, 0, (cudaStream_t)stream>>>(g, (const bf16*)y, rows, C, csg,
+                                                                  csy, act, (bf16*)gb, csb);
+  return launched("act_bwd");
+}
+
+ddflb_status ddflb_nn_bias_grad(const float* g, int64_t rows, int32_t C, int32_t cs, float* db,
+                                void* stream) {
+  if (!g || !db || rows <= 0 || C <= 0) return bad("bias_grad: bad args");
+  k_bias_grad<<<C, 256, 0, (cudaStream_t)stream>>>(g, rows, C, cs, db);
+  return launched("bias_grad");
+}
+
+ddflb_status ddflb_nn_mse(const float* pred, const float* target, int64_t n, float* grad,
+                          double* dev_partial, double* dev_loss, void* stream) {
+  if (!pred || !target || !dev_partial || !dev_loss || n <= 0) return bad("mse: bad args");
+  const int nb = 256;  // dev_partial holds 256 doubles
+  k_mse<<<nb, 256, 0, (cudaStream_t)stream>>>(pred, target, n, grad, dev_partial);
+  k_sum<<<1, 32, 0, (cudaStream_t)stream>>>(dev_partial, nb, 1.0 / (double)n, dev_loss);
+  return launched("mse");
+}
+
+ddflb_status ddflb_nn_adam(float* w, const float* g, float* m, float* v, void* wb, int64_t n,
+                           float lr, float beta1, float beta2, float eps, int64_t t, float wd,
+                           void* stream) {
+  if (!w || !g || !m || !v || n <= 0 || t < 1) return bad("adam: bad args");
+  const float c1 = 1.f - powf(beta1, (float)t), c2 = 1.f - powf(beta2, (float)t);
+  k_adam<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(w, g, m, v, (bf16*)wb, n, lr, beta1,
+                                                         beta2, eps, c1, c2, wd);
+  return launched("adam");
+}
+
+ddflb_status ddflb_nn_cast_bf16(const float* x, int64_t rows, int32_t C, int32_t csx, void* y,
+                                int32_t csy, void* stream) {
+  if (!x || !y || rows <= 0 || C <= 0) return bad("cast: bad args");
+  k_cast_bf16<<<grid_for(rows * C), 256, 0, (cudaStream_t)stream>>>(x, rows, C, csx, (bf16*)y,
+                                                                    csy);
+  return launched("cast");
+}
+
+}  // extern "C"

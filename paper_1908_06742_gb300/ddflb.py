@@ -88,6 +88,28 @@ SIGNATURES = {
     "ddflb_autotune": (ctypes.c_int, [_VP, ctypes.c_int32] + [ctypes.POINTER(ctypes.c_int32)] * 2 +
                        [ctypes.POINTER(ctypes.c_double)]),
     "ddflb_set_block": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32]),
+    # warm-start surrogate network kernels
+    "ddflb_nn_gemm": (ctypes.c_int, [_FP, _FP] + [ctypes.c_int32] * 5 +
+                      [_FP, ctypes.c_int32, _FP, ctypes.c_int32, _FP] + [ctypes.c_int32] * 3 +
+                      [_FP, _VP]),
+    "ddflb_nn_im2col": (ctypes.c_int, [_FP] + [ctypes.c_int32] * 5 + [_FP, ctypes.c_int32, _VP]),
+    "ddflb_nn_col2im": (ctypes.c_int, [_FP] + [ctypes.c_int32] * 4 + [_FP, ctypes.c_int32, _VP]),
+    "ddflb_nn_transpose": (ctypes.c_int, [_FP] + [ctypes.c_int32] * 3 + [_FP, _VP]),
+    "ddflb_nn_pool": (ctypes.c_int, [_FP] + [ctypes.c_int32] * 5 + [_FP, ctypes.c_int32, _VP]),
+    "ddflb_nn_pool_bwd": (ctypes.c_int, [_FP] + [ctypes.c_int32] * 5 +
+                          [_FP, ctypes.c_int32, ctypes.c_int32, _VP]),
+    "ddflb_nn_upsample": (ctypes.c_int, [_FP] + [ctypes.c_int32] * 5 + [_FP, ctypes.c_int32, _VP]),
+    "ddflb_nn_upsample_bwd": (ctypes.c_int, [_FP] + [ctypes.c_int32] * 5 +
+                              [_FP, ctypes.c_int32, _VP]),
+    "ddflb_nn_act_bwd": (ctypes.c_int, [_FP, _FP, ctypes.c_int64] + [ctypes.c_int32] * 4 +
+                         [_FP, ctypes.c_int32, _VP]),
+    "ddflb_nn_bias_grad": (ctypes.c_int, [_FP, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                          _FP, _VP]),
+    "ddflb_nn_mse": (ctypes.c_int, [_FP, _FP, ctypes.c_int64, _FP, _FP, _FP, _VP]),
+    "ddflb_nn_adam": (ctypes.c_int, [_FP, _FP, _FP, _FP, _FP, ctypes.c_int64] +
+                      [ctypes.c_float] * 4 + [ctypes.c_int64, ctypes.c_float, _VP]),
+    "ddflb_nn_cast_bf16": (ctypes.c_int, [_FP, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                          _FP, ctypes.c_int32, _VP]),
     "ddflb_batch_destroy": (ctypes.c_int, [_VP]),
     "ddflb_last_error": (ctypes.c_char_p, []),
     "ddflb_version": (ctypes.c_char_p, []),

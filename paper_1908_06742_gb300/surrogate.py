@@ -1,0 +1,391 @@
+"""Learned warm start for lid-driven cavities.
+
+A small U-Net (about 1M parameters, BF16 weights and activations, FP32
+accumulation and master weights) maps the flow parameters (Re, Pe, lid speed)
+and the node coordinates to the steady fields (u_x, u_y, phi, omega, and the
+density rho for a consistent pressure).  The prediction only initialises the
+populations -- equilibrium plus the Chapman-Enskog non-equilibrium part implied
+by the predicted gradients -- and the lattice Boltzmann method then runs to the
+residual tolerance exactly as from a cold start, so the method stays the judge
+of the surrogate.  Training data are steady solutions the method itself
+produces (batched runs to the tolerance).
+
+Every arithmetic step runs in libddflb's kernels (tensor-core GEMM, im2col,
+pooling, ...): this module sequences the calls and owns the buffers (allocated
+with PyTorch).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import ddflb as D
+
+CIN, COUT = 16, 8            # padded input / output channels (5 and 5 used)
+LEAKY = 1
+
+
+def specs(c: int, cin: int = CIN, cout: int = COUT):
+    """(name, input channels, output channels) of the U-Net's convolutions."""
+    return [("e1a", cin, c), ("e1b", c, c), ("e2a", c, 2 * c), ("e2b", 2 * c, 2 * c),
+            ("e3a", 2 * c, 4 * c), ("e3b", 4 * c, 4 * c), ("b1", 4 * c, 4 * c),
+            ("b2", 4 * c, 4 * c), ("d3a", 8 * c, 4 * c), ("d3b", 4 * c, 2 * c),
+            ("d2a", 4 * c, 2 * c), ("d2b", 2 * c, c), ("d1a", 2 * c, c), ("d1b", c, c),
+            ("head", c, cout)]
+
+
+def _ck(status):
+    D._check(status)
+
+
+@dataclass
+class _V:
+    """A channel slice of an NHWC buffer."""
+    t: object      # torch tensor [B, H, W, cs]
+    off: int       # first channel
+    C: int         # channels in the slice
+
+    @property
+    def cs(self):
+        return self.t.shape[-1]
+
+    @property
+    def ptr(self):
+        return self.t.data_ptr() + self.off * self.t.element_size()
+
+
+class UNet:
+    def __init__(self, c=32, batch=16, H=128, W=128, device="cuda", seed=0, stream=None):
+        import torch
+        assert H % 8 == 0 and W % 8 == 0
+        self.torch = torch
+        self.c, self.B, self.H, self.W = c, batch, H, W
+        self.dev = torch.device(device)
+        self.lib = D.load()
+        self.stream = stream or torch.cuda.current_stream(self.dev)
+        self.s = self.stream.cuda_stream
+        self.specs = specs(c)
+        self.numel = 0
+        gen = torch.Generator().manual_seed(seed)
+        f32 = dict(dtype=torch.float32, device=self.dev)
+        self.p = {}
+        for name, ci, co in self.specs:
+            k = ci if name == "head" else 9 * ci
+            std = math.sqrt((1.0 if name == "head" else 2.0) / k)
+            w = (torch.randn(co, k, generator=gen, dtype=torch.float64) * std).float().to(self.dev)
+            b = torch.zeros(co, **f32) if name == "head" else \
+                (0.01 * torch.randn(co, generator=gen, dtype=torch.float64)).float().to(self.dev)
+            self.p[name] = {
+                "w": w, "b": b, "wb": w.to(torch.bfloat16), "gw": torch.zeros_like(w),
+                "gb": torch.zeros_like(b), "mw": torch.zeros_like(w), "vw": torch.zeros_like(w),
+                "mb": torch.zeros_like(b), "vb": torch.zeros_like(b),
+                "wT": torch.empty(k, co, dtype=torch.bfloat16, device=self.dev), "ci": ci, "co": co}
+            self.numel += w.numel() + b.numel()
+        self.t = 0
+        self._alloc()
+
+    # ------------------------------------------------------------------ buffers
+    def _alloc(self):
+        torch, B, c = self.torch, self.B, self.c
+        H, W = self.H, self.W
+        L = [(H, W), (H // 2, W // 2), (H // 4, W // 4), (H // 8, W // 8)]
+        self.L = L
+        bf = lambda lv, ch: torch.zeros(B, *L[lv], ch, dtype=torch.bfloat16, device=self.dev)
+        f32 = lambda lv, ch: torch.zeros(B, *L[lv], ch, dtype=torch.float32, device=self.dev)
+        A = self.a = {}
+        A["x"] = bf(0, CIN)
+        for name, lv, ch in [("e1a", 0, c), ("cat1", 0, 2 * c), ("p1", 1, c), ("e2a", 1, 2 * c),
+                             ("cat2", 1, 4 * c), ("p2", 2, 2 * c), ("e3a", 2, 4 * c),
+                             ("cat3", 2, 8 * c), ("p3", 3, 4 * c), ("b1", 3, 4 * c),
+                             ("b2", 3, 4 * c), ("d3a", 2, 4 * c), ("d3b", 2, 2 * c),
+                             ("d2a", 1, 2 * c), ("d2b", 1, c), ("d1a", 0, c), ("d1b", 0, c)]:
+            A[name] = bf(lv, ch)
+        G = self.g = {k: f32(lv, v.shape[-1]) for k, v in A.items() if k != "x"
+                      for lv in [next(i for i, s in enumerate(L) if s == tuple(v.shape[1:3]))]}
+        self.out = f32(0, COUT)
+        self.gout = f32(0, COUT)
+        V = lambda d, n, off=0, C=None: _V(d[n], off, C if C is not None else d[n].shape[-1] - off)
+        # conv layer wiring: (name, level, input view, output view, grad-in view, grad-out view)
+        self.layers = [
+            ("e1a", 0, V(A, "x"), V(A, "e1a"), None, V(G, "e1a")),
+            ("e1b", 0, V(A, "e1a"), V(A, "cat1", c), V(G, "e1a"), V(G, "cat1", c)),
+            ("e2a", 1, V(A, "p1"), V(A, "e2a"), V(G, "p1"), V(G, "e2a")),
+            ("e2b", 1, V(A, "e2a"), V(A, "cat2", 2 * c), V(G, "e2a"), V(G, "cat2", 2 * c)),
+            ("e3a", 2, V(A, "p2"), V(A, "e3a"), V(G, "p2"), V(G, "e3a")),
+            ("e3b", 2, V(A, "e3a"), V(A, "cat3", 4 * c), V(G, "e3a"), V(G, "cat3", 4 * c)),
+            ("b1", 3, V(A, "p3"), V(A, "b1"), V(G, "p3"), V(G, "b1")),
+            ("b2", 3, V(A, "b1"), V(A, "b2"), V(G, "b1"), V(G, "b2")),
+            ("d3a", 2, V(A, "cat3"), V(A, "d3a"), V(G, "cat3"), V(G, "d3a")),
+            ("d3b", 2, V(A, "d3a"), V(A, "d3b"), V(G, "d3a"), V(G, "d3b")),
+            ("d2a", 1, V(A, "cat2"), V(A, "d2a"), V(G, "cat2"), V(G, "d2a")),
+            ("d2b", 1, V(A, "d2a"), V(A, "d2b"), V(G, "d2a"), V(G, "d2b")),
+            ("d1a", 0, V(A, "cat1"), V(A, "d1a"), V(G, "cat1"), V(G, "d1a")),
+            ("d1b", 0, V(A, "d1a"), V(A, "d1b"), V(G, "d1a"), V(G, "d1b")),
+        ]
+        P0 = B * H * W
+        kmax = max(9 * ci for n, ci, co in self.specs if n != "head")
+        ci_of = {n: ci for n, ci, _ in self.specs}
+        need = max(B * L[lv][0] * L[lv][1] * 9 * ci_of[n] for n, lv, *_ in self.layers)
+        self.col = torch.empty(need, dtype=torch.bfloat16, device=self.dev)
+        self.colT = torch.empty(need, dtype=torch.bfloat16, device=self.dev)
+        self.dcol = torch.empty(need, dtype=torch.float32, device=self.dev)
+        comax = max(co for _, _, co in self.specs)
+        self.gbf = torch.empty(P0 * comax, dtype=torch.bfloat16, device=self.dev)
+        self.gbT = torch.empty(P0 * comax, dtype=torch.bfloat16, device=self.dev)
+        self.xT = torch.empty(P0 * c, dtype=torch.bfloat16, device=self.dev)
+        self.splits_max = 48
+        self.partial = torch.empty(self.splits_max * comax * kmax, dtype=torch.float32,
+                                   device=self.dev)
+        self.mse_part = torch.empty(256, dtype=torch.float64, device=self.dev)
+        self.mse_loss = torch.empty(1, dtype=torch.float64, device=self.dev)
+
+    # ------------------------------------------------------------------ primitives
+    def _gemm(self, A, B, M, N, K, lda, ldb, Cf=0, ldc=0, Cb=0, ldcb=0, bias=0, act=0, acc=0,
+              splits=1):
+        _ck(self.lib.ddflb_nn_gemm(A, B, M, N, K, lda, ldb, Cf or None, ldc, Cb or None, ldcb,
+                                   bias or None, act, acc, splits,
+                                   self.partial.data_ptr() if splits > 1 else None, self.s))
+
+    def _splits(self, M, N, K):
+        tiles = ((M + 127) // 128) * ((N + 127) // 128)
+        s = max(1, min(self.splits_max, 304 // max(tiles, 1), K // 2048))
+        return s
+
+    def _conv_fwd(self, name, lv, vin, vout):
+        p = self.p[name]
+        H, W = self.L[lv]
+        P, ci, co = self.B * H * W, p["ci"], p["co"]
+        assert vin.C == ci and vout.C == co
+        _ck(self.lib.ddflb_nn_im2col(vin.ptr, self.B, H, W, ci, vin.cs, self.col.data_ptr(), 0,
+                                     self.s))
+        self._gemm(self.col.data_ptr(), p["wb"].data_ptr(), P, co, 9 * ci, 9 * ci, 9 * ci,
+                   Cb=vout.ptr, ldcb=vout.cs, bias=p["b"].data_ptr(), act=LEAKY)
+
+    def _conv_bwd(self, name, lv, vin, vout, gin, gout):
+        p = self.p[name]
+        H, W = self.L[lv]
+        P, ci, co = self.B * H * W, p["ci"], p["co"]
+        gbf, gbT = self.gbf.data_ptr(), self.gbT.data_ptr()
+        # through the activation (derivative read from the stored output)
+        _ck(self.lib.ddflb_nn_act_bwd(gout.ptr, vout.ptr, P, co, gout.cs, vout.cs, LEAKY, gbf, co,
+                                      self.s))
+        _ck(self.lib.ddflb_nn_bias_grad(gout.ptr, P, co, gout.cs, p["gb"].data_ptr(), self.s))
+        # dW [co][9ci] = g^T . im2col(x)
+        _ck(self.lib.ddflb_nn_transpose(gbf, P, co, co, gbT, self.s))
+        _ck(self.lib.ddflb_nn_im2col(vin.ptr, self.B, H, W, ci, vin.cs, self.colT.data_ptr(), 1,
+                                     self.s))
+        self._gemm(gbT, self.colT.data_ptr(), co, 9 * ci, P, P, P, Cf=p["gw"].data_ptr(),
+                   ldc=9 * ci, splits=self._splits(co, 9 * ci, P))
+        if gin is None:
+            return
+        # dX = col2im(g . W)
+        _ck(self.lib.ddflb_nn_transpose(p["wb"].data_ptr(), co, 9 * ci, 9 * ci,
+                                        p["wT"].data_ptr(), self.s))
+        self._gemm(gbf, p["wT"].data_ptr(), P, 9 * ci, co, co, co, Cf=self.dcol.data_ptr(),
+                   ldc=9 * ci)
+        _ck(self.lib.ddflb_nn_col2im(self.dcol.data_ptr(), self.B, H, W, ci, gin.ptr, gin.cs,
+                                     self.s))
+
+    def _pool(self, src, lv, dst):
+        H, W = self.L[lv]
+        _ck(self.lib.ddflb_nn_pool(src.ptr, self.B, H, W, src.C, src.cs, dst.ptr, dst.cs, self.s))
+
+    def _up(self, src, lv, dst):
+        H, W = self.L[lv]  # source (coarse) level
+        _ck(self.lib.ddflb_nn_upsample(src.ptr, self.B, H, W, src.C, src.cs, dst.ptr, dst.cs,
+                                       self.s))
+
+    # ------------------------------------------------------------------ network
+    def forward(self, x=None):
+        """x: BF16 [B, H, W, 16] (copied into the input buffer if given).
+        Returns the FP32 output [B, H, W, 8]."""
+        if x is not None:
+            self.a["x"].copy_(x)
+        A, c, Ly = self.a, self.c, {n: (lv, vi, vo) for n, lv, vi, vo, _, _ in self.layers}
+        cv = lambda n: self._conv_fwd(n, *Ly[n])
+        cv("e1a"); cv("e1b")
+        self._pool(_V(A["cat1"], c, c), 0, _V(A["p1"], 0, c))
+        cv("e2a"); cv("e2b")
+        self._pool(_V(A["cat2"], 2 * c, 2 * c), 1, _V(A["p2"], 0, 2 * c))
+        cv("e3a"); cv("e3b")
+        self._pool(_V(A["cat3"], 4 * c, 4 * c), 2, _V(A["p3"], 0, 4 * c))
+        cv("b1"); cv("b2")
+        self._up(_V(A["b2"], 0, 4 * c), 3, _V(A["cat3"], 0, 4 * c))
+        cv("d3a"); cv("d3b")
+        self._up(_V(A["d3b"], 0, 2 * c), 2, _V(A["cat2"], 0, 2 * c))
+        cv("d2a"); cv("d2b")
+        self._up(_V(A["d2b"], 0, c), 1, _V(A["cat1"], 0, c))
+        cv("d1a"); cv("d1b")
+        p = self.p["head"]
+        P = self.B * self.H * self.W
+        self._gemm(A["d1b"].data_ptr(), p["wb"].data_ptr(), P, COUT, c, c, c,
+                   Cf=self.out.data_ptr(), ldc=COUT, bias=p["b"].data_ptr(), act=0)
+        return self.out
+
+    def backward(self, target):
+        """MSE loss against target (FP32 [B, H, W, 8]); fills every gradient.
+        Returns the loss as a device scalar (FP64)."""
+        G, A, c = self.g, self.a, self.c
+        n = self.out.numel()
+        _ck(self.lib.ddflb_nn_mse(self.out.data_ptr(), target.data_ptr(), n,
+                                  self.gout.data_ptr(), self.mse_part.data_ptr(),
+                                  self.mse_loss.data_ptr(), self.s))
+        P = self.B * self.H * self.W
+        p = self.p["head"]
+        gbf, gbT = self.gbf.data_ptr(), self.gbT.data_ptr()
+        _ck(self.lib.ddflb_nn_cast_bf16(self.gout.data_ptr(), P, COUT, COUT, gbf, COUT, self.s))
+        _ck(self.lib.ddflb_nn_bias_grad(self.gout.data_ptr(), P, COUT, COUT, p["gb"].data_ptr(),
+                                        self.s))
+        _ck(self.lib.ddflb_nn_transpose(gbf, P, COUT, COUT, gbT, self.s))
+        _ck(self.lib.ddflb_nn_transpose(A["d1b"].data_ptr(), P, c, c, self.xT.data_ptr(), self.s))
+        self._gemm(gbT, self.xT.data_ptr(), COUT, c, P, P, P, Cf=p["gw"].data_ptr(), ldc=c,
+                   splits=self._splits(COUT, c, P))
+        _ck(self.lib.ddflb_nn_transpose(p["wb"].data_ptr(), COUT, c, c, p["wT"].data_ptr(), self.s))
+        self._gemm(gbf, p["wT"].data_ptr(), P, c, COUT, COUT, COUT, Cf=G["d1b"].data_ptr(), ldc=c)
+        Ly = {n: (lv, vi, vo, gi, go) for n, lv, vi, vo, gi, go in self.layers}
+        cb = lambda n: self._conv_bwd(n, *Ly[n])
+        cb("d1b"); cb("d1a")
+        H1, W1 = self.L[1]
+        up_b = lambda g_src, lv, dst: _ck(self.lib.ddflb_nn_upsample_bwd(
+            g_src.ptr, self.B, *self.L[lv], g_src.C, g_src.cs, dst.ptr, dst.cs, self.s))
+        pool_b = lambda g_src, lv, dst: _ck(self.lib.ddflb_nn_pool_bwd(
+            g_src.ptr, self.B, *self.L[lv], g_src.C, g_src.cs, dst.ptr, dst.cs, 1, self.s))
+        up_b(_V(G["cat1"], 0, c), 1, _V(G["d2b"], 0, c))
+        cb("d2b"); cb("d2a")
+        up_b(_V(G["cat2"], 0, 2 * c), 2, _V(G["d3b"], 0, 2 * c))
+        cb("d3b"); cb("d3a")
+        up_b(_V(G["cat3"], 0, 4 * c), 3, _V(G["b2"], 0, 4 * c))
+        cb("b2"); cb("b1")
+        pool_b(_V(G["p3"], 0, 4 * c), 2, _V(G["cat3"], 4 * c, 4 * c))
+        cb("e3b"); cb("e3a")
+        pool_b(_V(G["p2"], 0, 2 * c), 1, _V(G["cat2"], 2 * c, 2 * c))
+        cb("e2b"); cb("e2a")
+        pool_b(_V(G["p1"], 0, c), 0, _V(G["cat1"], c, c))
+        cb("e1b"); cb("e1a")
+        return self.mse_loss
+
+    def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, wd=0.0):
+        self.t += 1
+        for name, _, _ in self.specs:
+            p = self.p[name]
+            _ck(self.lib.ddflb_nn_adam(p["w"].data_ptr(), p["gw"].data_ptr(), p["mw"].data_ptr(),
+                                       p["vw"].data_ptr(), p["wb"].data_ptr(), p["w"].numel(), lr,
+                                       beta1, beta2, eps, self.t, wd, self.s))
+            _ck(self.lib.ddflb_nn_adam(p["b"].data_ptr(), p["gb"].data_ptr(), p["mb"].data_ptr(),
+                                       p["vb"].data_ptr(), None, p["b"].numel(), lr, beta1, beta2,
+                                       eps, self.t, 0.0, self.s))
+
+    # ------------------------------------------------------------------ exchange
+    def get_params(self):
+        """FP32 master weights as numpy, in the oracle's layout (W[Co][3][3][Ci])."""
+        out = {}
+        for name, ci, co in self.specs:
+            p = self.p[name]
+            w = p["w"].double().cpu().numpy()
+            out[name] = (w if name == "head" else w.reshape(co, 3, 3, ci),
+                         p["b"].double().cpu().numpy())
+        return out
+
+    def grads(self):
+        out = {}
+        for name, ci, co in self.specs:
+            p = self.p[name]
+            g = p["gw"].double().cpu().numpy()
+            out[name] = (g if name == "head" else g.reshape(co, 3, 3, ci),
+                         p["gb"].double().cpu().numpy())
+        return out
+
+
+# ---------------------------------------------------------------------- data
+RE_RANGE, PE_RANGE, U_RANGE = (100.0, 3200.0), (50.0, 3200.0), (0.05, 0.1)
+
+
+def draws(n: int, seed: int):
+    """Seeded cavity parameters: Re log-uniform [100, 3200], Pe log-uniform
+    [50, 3200], lid speed uniform [0.05, 0.1]."""
+    r = np.random.default_rng(seed)
+    lg = lambda lo, hi: np.exp(r.uniform(math.log(lo), math.log(hi), n))
+    return [dict(re=float(a), pe=float(b), u=float(c))
+            for a, b, c in zip(lg(*RE_RANGE), lg(*PE_RANGE), r.uniform(*U_RANGE, n))]
+
+
+def cavity_config(d, n, check=1000):
+    """Lattice parameters of one cavity: nu = U L / Re, D = U L / Pe, L = n."""
+    w = D.relaxation_rate(d["u"] * n / d["re"])
+    wg = D.relaxation_rate(d["u"] * n / d["pe"])
+    return D.Config(nx=n, ny=n, bc="cavity", u_lid=d["u"], phi_lid=1.0, phi_wall=0.0,
+                    omega_f=(0, 0, 0, 1.2, w, w, 1.2, 1.2, 1.2),
+                    omega_g=(0, wg, wg, 1.2, 1.2, 1.2, 1.2, 1.2, 1.2), check_every=check)
+
+
+def run_to_steady(cfgs, starts, tol=1e-8, chunk=2000, max_steps=2_000_000, device="cuda"):
+    """Advance cavities (one batch) until every residual is below tol or the
+    step cap; starts[i] = (rho, ux, uy, phi, grads).  Returns the batch and
+    its stats."""
+    b = D.Batch(cfgs, device=device).set_run(tol=tol, steps_per_launch=chunk)
+    b.autotune(trial_steps=4, cache=True)
+    for i, s in enumerate(starts):
+        b.init(i, *s)
+    done = 0
+    while done < max_steps:
+        b.step(chunk * 10)
+        done += chunk * 10
+        st = b.stats()
+        if (st["flags"] != 0).all():
+            break
+    return b, b.stats()
+
+
+def input_planes(d, n, xp=np):
+    """Network input: normalised log Re, log Pe, lid speed and coordinates,
+    zero-padded to 16 channels ([n, n, 16])."""
+    lr = (math.log(d["re"]) - 0.5 * sum(map(math.log, RE_RANGE))) / (0.5 * math.log(RE_RANGE[1] / RE_RANGE[0]))
+    lp = (math.log(d["pe"]) - 0.5 * sum(map(math.log, PE_RANGE))) / (0.5 * math.log(PE_RANGE[1] / PE_RANGE[0]))
+    lu = (d["u"] - 0.075) / 0.025
+    x = np.zeros((n, n, CIN), np.float32)
+    g = (np.arange(n) + 0.5) / n * 2 - 1
+    x[..., 0], x[..., 1], x[..., 2] = lr, lp, lu
+    x[..., 3] = g[None, :]
+    x[..., 4] = g[:, None]
+    return x
+
+
+OMEGA_SCALE = 20.0  # omega L / U spans a few tens in the cavity interior
+
+
+def targets(fields, d, n):
+    """Network target from steady fields: (ux/U, uy/U, phi, omega n / (U s),
+    (rho - 1) / U^2), zero-padded to 8 channels."""
+    U = d["u"]
+    t = np.zeros((n, n, COUT), np.float32)
+    t[..., 0] = fields["ux"] / U
+    t[..., 1] = fields["uy"] / U
+    t[..., 2] = fields["phi"]
+    om = np.nan_to_num(fields["omega"], nan=0.0)
+    t[..., 3] = np.clip(om * n / U / OMEGA_SCALE, -5, 5)
+    t[..., 4] = (fields["rho"] - 1.0) / (U * U)
+    return t
+
+
+def warm_start(pred, d, n):
+    """Initial fields from a prediction [n, n, 8]: velocity, scalar, density and
+    the gradients for the non-equilibrium part.  Diagonal derivatives and S_xy
+    come from central differences of the predicted velocity (initial state
+    only); the antisymmetric part from the predicted vorticity."""
+    U = d["u"]
+    ux = pred[..., 0] * U
+    uy = pred[..., 1] * U
+    phi = np.clip(pred[..., 2], 0.0, 1.0)
+    om = pred[..., 3] * OMEGA_SCALE * U / n
+    rho = 1.0 + pred[..., 4] * U * U
+    dyux, dxux = np.gradient(ux)
+    dyuy, dxuy = np.gradient(uy)
+    sxy = 0.5 * (dxuy + dyux)
+    dxuy, dyux = sxy + 0.5 * om, sxy - 0.5 * om
+    dyphi, dxphi = np.gradient(phi)
+    grads = np.stack([dxux, dyux, dxuy, dyuy, dxphi, dyphi]).astype(np.float32)
+    f = lambda a: np.ascontiguousarray(a, np.float32)
+    return f(rho), f(ux), f(uy), f(phi), f(grads)

@@ -1,0 +1,128 @@
+"""Surrogate network kernels against FP64 references: the tensor-core GEMM
+against a float64 matrix product of the same BF16 inputs, and the full U-Net
+(output and every parameter gradient) against the FP64 network oracle run on
+the GPU's BF16 weights and input.  BF16 rounding of the activations between
+layers bounds the agreement (about 2^-9 per layer)."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import unet as OU
+from paper_1908_06742_gb300 import build as B
+from paper_1908_06742_gb300 import ddflb as D
+from paper_1908_06742_gb300 import surrogate as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    B.build()
+    D.load()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+@pytest.mark.parametrize("M,N,K,splits,bias,act", [
+    (1, 1, 8, 1, False, 0), (130, 70, 40, 1, True, 1), (257, 129, 136, 1, True, 0),
+    (1000, 64, 4096, 7, False, 0), (64, 2304, 8192, 16, True, 1), (300, 8, 32, 1, True, 0)])
+def test_gemm_against_float64(M, N, K, splits, bias, act):
+    g = torch.Generator().manual_seed(M * 7 + N)
+    A = torch.randn(M, K, generator=g).to(torch.bfloat16).cuda()
+    Bm = torch.randn(N, K, generator=g).to(torch.bfloat16).cuda()
+    b = torch.randn(N, generator=g).float().cuda() if bias else None
+    Cf = torch.empty(M, N, device="cuda")
+    Cb = torch.empty(M, N, dtype=torch.bfloat16, device="cuda") if splits == 1 else None
+    part = torch.empty(splits * M * N, device="cuda") if splits > 1 else None
+    lib = D.load()
+    D._check(lib.ddflb_nn_gemm(A.data_ptr(), Bm.data_ptr(), M, N, K, K, K, Cf.data_ptr(), N,
+                               Cb.data_ptr() if Cb is not None else None, N,
+                               b.data_ptr() if b is not None else None, act, 0, splits,
+                               part.data_ptr() if part is not None else None,
+                               torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    ref = A.double().cpu().numpy() @ Bm.double().cpu().numpy().T
+    if bias:
+        ref = ref + b.double().cpu().numpy()
+    if act == 1:
+        ref = np.where(ref > 0, ref, 0.02 * ref)
+    got = Cf.double().cpu().numpy()
+    # FP32 accumulation of exact BF16 products: relative error ~ sqrt(K) * 2^-24
+    assert np.abs(got - ref).max() <= 1e-5 * (np.abs(ref).max() + 1) * max(1, math.sqrt(K / 64)), \
+        np.abs(got - ref).max()
+    if Cb is not None:
+        assert rel(Cb.double().cpu().numpy(), ref) < 4e-3
+
+
+def test_gemm_rejects_bad_shapes():
+    lib = D.load()
+    st = lib.ddflb_nn_gemm(16, 16, 4, 4, 12, 12, 12, 16, 4, None, 0, None, 0, 0, 1, None, None)
+    assert st == D.EINVAL and b"multiples of 8" in lib.ddflb_last_error()
+
+
+def make_net(c=8, batch=2, H=16, seed=0):
+    net = S.UNet(c=c, batch=batch, H=H, W=H, seed=seed)
+    r = np.random.default_rng(seed + 1)
+    x = np.zeros((batch, H, H, S.CIN), np.float32)
+    x[..., :5] = r.standard_normal((batch, H, H, 5))
+    t = np.zeros((batch, H, H, S.COUT), np.float32)
+    t[..., :5] = r.standard_normal((batch, H, H, 5))
+    xb = torch.from_numpy(x).to(torch.bfloat16).cuda()
+    return net, xb, torch.from_numpy(t).cuda()
+
+
+def oracle_params(net):
+    """The GPU's BF16 weights (what its GEMMs use) and FP32 biases, in FP64."""
+    P = {}
+    for name, ci, co in net.specs:
+        p = net.p[name]
+        w = p["wb"].double().cpu().numpy()
+        P[name] = (w if name == "head" else w.reshape(co, 3, 3, ci), p["b"].double().cpu().numpy())
+    return P
+
+
+def test_unet_forward_and_gradients_match_oracle():
+    net, xb, t = make_net()
+    out = net.forward(xb)
+    loss = net.backward(t)
+    torch.cuda.synchronize()
+    P = oracle_params(net)
+    x64 = xb.double().cpu().numpy()
+    ref_out, cache = OU.forward(P, x64)
+    G = OU.backward(P, cache, ref_out, t.double().cpu().numpy())
+    e_out = rel(out.double().cpu().numpy(), ref_out)
+    assert e_out < 2e-2, e_out
+    assert abs(float(loss.item()) - OU.loss(ref_out, t.double().cpu().numpy())) < 2e-2 * float(loss.item())
+    got = net.grads()
+    worst = {}
+    for name, _, _ in net.specs:
+        for k in (0, 1):
+            worst[(name, k)] = rel(got[name][k], G[name][k])
+    print("gradient relative errors", {f"{n}{'.b' if k else '.w'}": round(v, 4) for (n, k), v in worst.items()})
+    assert max(worst.values()) < 6e-2, worst
+
+
+def test_training_reduces_loss():
+    """A few hundred Adam steps on a fixed smooth target: the loss falls by an
+    order of magnitude (the network and its gradients are wired correctly)."""
+    net, xb, _ = make_net(c=8, batch=4, H=32, seed=3)
+    H = 32
+    yy, xx = np.meshgrid(np.linspace(-1, 1, H), np.linspace(-1, 1, H), indexing="ij")
+    t = np.zeros((4, H, H, S.COUT), np.float32)
+    for k in range(4):
+        t[k, ..., 0] = np.sin(np.pi * xx * (k + 1) / 2) * yy
+        t[k, ..., 1] = np.cos(np.pi * yy) * 0.5
+    tt = torch.from_numpy(t).cuda()
+    first = None
+    for it in range(400):
+        net.forward(xb)
+        loss = float(net.backward(tt).item())
+        first = first if first is not None else loss
+        net.adam(lr=3e-3)
+    assert loss < 0.1 * first, (first, loss)
