@@ -228,9 +228,11 @@ size_t ddflb_batch_workspace_bytes(int32_t n, const ddflb_params* p);
 ddflb_status ddflb_batch_create(int32_t n, const ddflb_params* p, void* dev_workspace,
                                 size_t bytes, void* cuda_stream, ddflb_batch** out);
 /* Tolerance for the convergence freeze (0 = never freeze on convergence),
- * steps per persistent launch, and the barrier wait limit in seconds. */
+ * steps per persistent launch, the barrier wait limit in seconds, and whether
+ * the freeze also waits for the scalar residual |phi(t)-phi(t-K)|/(K |phi(t)|)
+ * to fall below tol (the vorticity of Sec. 4 depends on the scalar lattice). */
 ddflb_status ddflb_batch_set_run(ddflb_batch* b, double tol, int32_t steps_per_launch,
-                                 double barrier_timeout_s);
+                                 double barrier_timeout_s, int32_t scalar_residual);
 /* Tile shape (32x4, 64x2, 128x1, 32x8, 64x4, 128x2, 256x1) and CTAs per SM
  * (0 = as many as fit); rebuilds the tile list.  Used by the autotuner. */
 ddflb_status ddflb_batch_set_tiles(ddflb_batch* b, int32_t tile_x, int32_t tile_y,

@@ -33,10 +33,13 @@
 
 namespace ddflb {
 
+// per-tile sums of a check: |u|^2, |u - u_prev|^2, rho - rho0, phi^2, (phi - phi_prev)^2
+constexpr int kParts = 5;
+
 struct BatchInst {
   LbParams P;
   void* buf[2];  // f planes; g planes follow 9 planes later
-  float* uprev;  // 2 planes [ny][nx]
+  float* uprev;  // 3 planes [ny][nx]: u_x, u_y, phi
   int64_t goff;  // element offset of the g planes from the f planes
   int32_t tile_begin, tile_end;
   int32_t bc;
@@ -44,7 +47,8 @@ struct BatchInst {
 };
 
 struct BatchStatus {
-  double residual;
+  double residual;      // the residual the freeze decision uses
+  double residual_phi;  // |phi(t) - phi(t-K)| / (K |phi(t)|)
   double u2;
   double mass_dev;
   int64_t steps_to_tol;  // state time at which the residual first fell below tol (-1: not yet)
@@ -72,7 +76,8 @@ struct BatchArgs {
   int nsteps;
   int check_every;
   double tol;
-  double* part;  // 3 doubles per tile
+  int scalar_residual;  // freeze only when the scalar residual is below tol too
+  double* part;  // kParts doubles per tile
   BatchStatus* ist;
   BatchSync* sync;
   long long timeout_ns;
@@ -124,7 +129,7 @@ __device__ bool grid_barrier(BatchSync* s, long long timeout_ns) {
 
 template <typename S, int BC>
 __device__ __forceinline__ void batch_cell(const LbParams& P, const BatchInst& I, int src, int x,
-                                           int y, bool snap, bool check, double acc[3]) {
+                                           int y, bool snap, bool check, double acc[kParts]) {
   const S* fin = (const S*)I.buf[src];
   const S* gin = fin + I.goff;
   S* fout = (S*)I.buf[src ^ 1];
@@ -145,13 +150,17 @@ __device__ __forceinline__ void batch_cell(const LbParams& P, const BatchInst& I
     const int64_t c = (int64_t)y * P.nx + x, n = (int64_t)P.nx * P.ny;
     if (check) {
       const double ex = (double)q.ux - I.uprev[c], ey = (double)q.uy - I.uprev[n + c];
+      const double ep = (double)q.phi - I.uprev[2 * n + c];
       acc[0] += (double)q.ux * q.ux + (double)q.uy * q.uy;
       acc[1] += ex * ex + ey * ey;
       acc[2] += (double)mf.k0;
+      acc[3] += (double)q.phi * q.phi;
+      acc[4] += ep * ep;
     }
     if (snap) {
       I.uprev[c] = q.ux;
       I.uprev[n + c] = q.uy;
+      I.uprev[2 * n + c] = q.phi;
     }
   }
 }
@@ -206,7 +215,7 @@ __global__ void __launch_bounds__(256) k_batch(BatchArgs A) {
       if (!sActive) continue;
       const bool check = check_t && t - A.check_every >= sInit;
       const int x = T.y + threadIdx.x % A.tile_x, y = T.z + threadIdx.x / A.tile_x;
-      double acc[3] = {0.0, 0.0, 0.0};
+      double acc[kParts] = {0.0, 0.0, 0.0, 0.0, 0.0};
       if (x < sP.nx && y < sP.ny) {
         switch (sI.bc) {
           case BC_PERIODIC: batch_cell<S, BC_PERIODIC>(sP, sI, src, x, y, snap, check, acc); break;
@@ -215,9 +224,9 @@ __global__ void __launch_bounds__(256) k_batch(BatchArgs A) {
         }
       }
       if (check) {
-        for (int k = 0; k < 3; ++k) {
+        for (int k = 0; k < kParts; ++k) {
           const double v = block_sum(acc[k], sh);
-          if (threadIdx.x == 0) A.part[3 * (int64_t)tile + k] = v;
+          if (threadIdx.x == 0) A.part[kParts * (int64_t)tile + k] = v;
         }
       }
     }
@@ -227,18 +236,21 @@ __global__ void __launch_bounds__(256) k_batch(BatchArgs A) {
       for (int i = blockIdx.x; i < A.ninst; i += gridDim.x) {
         if (__ldcg(&A.ist[i].flags) != 0 || t - A.check_every < __ldcg(&A.ist[i].init_time)) continue;
         const int b = A.inst[i].tile_begin, e = A.inst[i].tile_end;
-        double v[3];
-        for (int k = 0; k < 3; ++k) {
+        double v[kParts];
+        for (int k = 0; k < kParts; ++k) {
           double a = 0.0;
-          for (int j = b + threadIdx.x; j < e; j += blockDim.x) a += __ldcg(&A.part[3 * (int64_t)j + k]);
+          for (int j = b + threadIdx.x; j < e; j += blockDim.x) a += __ldcg(&A.part[kParts * (int64_t)j + k]);
           v[k] = block_sum(a, sh);
         }
         if (threadIdx.x == 0) {
           BatchStatus& st = A.ist[i];
           st.u2 = v[0];
           st.mass_dev = v[2];
-          st.residual = v[0] > 0.0 ? sqrt(v[1] / v[0]) / A.check_every : 0.0;
-          if (!isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2])) {
+          const double ru = v[0] > 0.0 ? sqrt(v[1] / v[0]) / A.check_every : 0.0;
+          const double rp = v[3] > 0.0 ? sqrt(v[4] / v[3]) / A.check_every : 0.0;
+          st.residual_phi = rp;
+          st.residual = A.scalar_residual ? fmax(ru, rp) : ru;
+          if (!isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2]) || !isfinite(v[3])) {
             st.flags = DDFLB_INST_DIVERGED;
             st.state_time = t + 1;
           } else if (A.tol > 0.0 && st.residual < A.tol) {
@@ -306,14 +318,14 @@ BLayout blayout(int n, const ddflb_params* p) {
     const size_t bytes = al(18 * plane * esz(p[i].storage));
     L.off_buf0.push_back(o); o += bytes;
     L.off_buf1.push_back(o); o += bytes;
-    L.off_uprev.push_back(o); o += al(2 * (size_t)p[i].nx * p[i].ny * sizeof(float));
+    L.off_uprev.push_back(o); o += al(3 * (size_t)p[i].nx * p[i].ny * sizeof(float));
   }
   int mt = 0;
   for (int k = 0; k < kNumShapes; ++k) mt = std::max(mt, count_tiles(n, p, kShapes[k][0], kShapes[k][1]));
   L.max_tiles = mt;
   L.off_inst = o; o += al(n * sizeof(BatchInst));
   L.off_tiles = o; o += al((size_t)mt * sizeof(int4));
-  L.off_part = o; o += al((size_t)mt * 3 * sizeof(double));
+  L.off_part = o; o += al((size_t)mt * kParts * sizeof(double));
   L.off_status = o; o += al(n * sizeof(BatchStatus));
   L.off_sync = o; o += al(sizeof(BatchSync));
   L.total = o;
@@ -334,6 +346,7 @@ struct ddflb_batch {
   int ntiles;
   int chunk;
   double tol;
+  int scalar_residual;
   long long timeout_ns;
   int skip_block;
   int64_t step;  // host mirror of the global state time
@@ -415,6 +428,7 @@ BatchArgs args_for(ddflb_batch* b, int nsteps) {
   A.nsteps = nsteps;
   A.check_every = b->p[0].check_every;
   A.tol = b->tol;
+  A.scalar_residual = b->scalar_residual;
   A.part = b->d_part;
   A.ist = b->d_status;
   A.sync = b->d_sync;
@@ -550,11 +564,12 @@ ddflb_status ddflb_batch_create(int32_t n, const ddflb_params* p, void* ws, size
 }
 
 ddflb_status ddflb_batch_set_run(ddflb_batch* b, double tol, int32_t steps_per_launch,
-                                 double barrier_timeout_s) {
+                                 double barrier_timeout_s, int32_t scalar_residual) {
   if (!b) return bfail(DDFLB_EINVAL, "NULL batch");
   if (!(tol >= 0) || steps_per_launch < 1 || !(barrier_timeout_s > 0 && barrier_timeout_s <= 60))
     return bfail(DDFLB_EINVAL, "tol >= 0, steps_per_launch >= 1, timeout in (0, 60] s");
   b->tol = tol;
+  b->scalar_residual = scalar_residual != 0;
   b->chunk = steps_per_launch;
   b->timeout_ns = (long long)(barrier_timeout_s * 1e9);
   if (b->graph) {

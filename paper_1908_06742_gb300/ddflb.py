@@ -75,7 +75,8 @@ SIGNATURES = {
     "ddflb_batch_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32, ctypes.POINTER(Params)]),
     "ddflb_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(Params), _VP,
                                           ctypes.c_size_t, _VP, ctypes.POINTER(_VP)]),
-    "ddflb_batch_set_run": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_int32, ctypes.c_double]),
+    "ddflb_batch_set_run": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_int32, ctypes.c_double,
+                                           ctypes.c_int32]),
     "ddflb_batch_set_tiles": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "ddflb_batch_get_tiles": (ctypes.c_int, [_VP] + [ctypes.POINTER(ctypes.c_int32)] * 3),
     "ddflb_batch_init": (ctypes.c_int, [_VP, ctypes.c_int32, _FP, _FP, _FP, _FP, _FP]),
@@ -368,9 +369,9 @@ class Batch:
         self._h = h
         self._keep = {}
 
-    def set_run(self, tol=0.0, steps_per_launch=500, barrier_timeout_s=2.0):
+    def set_run(self, tol=0.0, steps_per_launch=500, barrier_timeout_s=2.0, scalar_residual=False):
         _check(self.lib.ddflb_batch_set_run(self._h, float(tol), int(steps_per_launch),
-                                            float(barrier_timeout_s)))
+                                            float(barrier_timeout_s), int(bool(scalar_residual))))
         return self
 
     def set_tiles(self, tile_x, tile_y, blocks_per_sm=0):

@@ -321,11 +321,14 @@ def cavity_config(d, n, check=1000):
                     omega_g=(0, wg, wg, 1.2, 1.2, 1.2, 1.2, 1.2, 1.2), check_every=check)
 
 
-def run_to_steady(cfgs, starts, tol=1e-8, chunk=2000, max_steps=2_000_000, device="cuda"):
-    """Advance cavities (one batch) until every residual is below tol or the
-    step cap; starts[i] = (rho, ux, uy, phi, grads).  Returns the batch and
+def run_to_steady(cfgs, starts, tol=1e-8, chunk=2000, max_steps=2_000_000, device="cuda",
+                  scalar_residual=True):
+    """Advance cavities (one batch) until every residual -- velocity and, by
+    default, scalar: the vorticity depends on both lattices -- is below tol or
+    the step cap; starts[i] = (rho, ux, uy, phi, grads).  Returns the batch and
     its stats."""
-    b = D.Batch(cfgs, device=device).set_run(tol=tol, steps_per_launch=chunk)
+    b = D.Batch(cfgs, device=device).set_run(tol=tol, steps_per_launch=chunk,
+                                             scalar_residual=scalar_residual)
     b.autotune(trial_steps=4, cache=True)
     for i, s in enumerate(starts):
         b.init(i, *s)
@@ -368,6 +371,114 @@ def targets(fields, d, n):
     t[..., 3] = np.clip(om * n / U / OMEGA_SCALE, -5, 5)
     t[..., 4] = (fields["rho"] - 1.0) / (U * U)
     return t
+
+
+def steady_fields(b, i):
+    f = b.fields(i, names=("rho", "ux", "uy", "phi", "omega"))
+    return {k: v.double().cpu().numpy() for k, v in f.items()}
+
+
+def train(net, X, T, epochs, lr=1e-3, seed=0, log=None):
+    """Adam on minibatches of (inputs X [N,n,n,16] BF16, targets T [N,n,n,8]
+    FP32), both on the device.  Returns the loss history (per epoch)."""
+    torch = net.torch
+    g = torch.Generator().manual_seed(seed)
+    hist = []
+    N = X.shape[0]
+    steps_per_epoch = max(1, N // net.B)
+    total = epochs * steps_per_epoch
+    k = 0
+    for ep in range(epochs):
+        perm = torch.randperm(N, generator=g)
+        acc = 0.0
+        for s in range(steps_per_epoch):
+            idx = perm[s * net.B:(s + 1) * net.B].to(X.device)
+            net.forward(X.index_select(0, idx))
+            loss = net.backward(T.index_select(0, idx).contiguous())
+            # cosine decay of the learning rate
+            net.adam(lr=lr * 0.5 * (1 + math.cos(math.pi * k / total)))
+            acc += float(loss.item()) if s == steps_per_epoch - 1 else 0.0
+            k += 1
+        hist.append(acc)
+        if log:
+            log(ep, acc)
+    return hist
+
+
+def predict(net, X):
+    """Network output for every sample of X (padded up to a whole batch)."""
+    torch = net.torch
+    outs = []
+    for s in range(0, X.shape[0], net.B):
+        xb = X[s:s + net.B]
+        if xb.shape[0] < net.B:
+            xb = torch.cat([xb, xb[:1].expand(net.B - xb.shape[0], *xb.shape[1:])])
+        outs.append(net.forward(xb).clone())
+    return torch.cat(outs)[:X.shape[0]]
+
+
+def experiment(n=128, n_train=512, n_test=64, epochs=60, batch=16, c=32, seed=1, tol=1e-8,
+               max_steps=2_000_000, device="cuda", log=print):
+    """The learned warm start, end to end: steady training data from the
+    method, GPU training, then held-out cavities run to the tolerance from a
+    cold start (rest) and from the network's prediction."""
+    import time
+    import torch
+    t0 = time.perf_counter()
+    tr, te = draws(n_train, seed), draws(n_test, seed + 1000)
+    rest = lambda: (np.ones((n, n), np.float32), np.zeros((n, n), np.float32),
+                    np.zeros((n, n), np.float32), np.zeros((n, n), np.float32), None)
+    # 1. training data: the method's own steady solutions (cold starts)
+    b, st = run_to_steady([cavity_config(d, n) for d in tr], [rest() for _ in tr], tol=tol,
+                          max_steps=max_steps, device=device)
+    ok = [i for i in range(len(tr)) if st["flags"][i] == D.INST_CONVERGED]
+    X = np.stack([input_planes(tr[i], n) for i in ok])
+    T = np.stack([targets(steady_fields(b, i), tr[i], n) for i in ok])
+    del b
+    t_data = time.perf_counter() - t0
+    log(f"data: {len(ok)}/{len(tr)} converged in {t_data:.1f} s")
+    # 2. training on the GPU with the library's kernels
+    net = UNet(c=c, batch=batch, H=n, W=n, device=device, seed=seed)
+    Xd = torch.from_numpy(X).to(torch.bfloat16).to(device)
+    Td = torch.from_numpy(T).to(device)
+    t1 = time.perf_counter()
+    hist = train(net, Xd, Td, epochs, log=lambda e, l: log(f"epoch {e} loss {l:.4e}") if e % 10 == 0 else None)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    # 3. held-out: cold start and warm start side by side in one batch
+    Xt = torch.from_numpy(np.stack([input_planes(d, n) for d in te])).to(torch.bfloat16).to(device)
+    pred = predict(net, Xt).cpu().numpy()
+    cfgs = [cavity_config(d, n) for d in te] * 2
+    starts = [rest() for _ in te] + [warm_start(pred[k], te[k], n) for k in range(len(te))]
+    b, st = run_to_steady(cfgs, starts, tol=tol, max_steps=max_steps, device=device)
+    rows = []
+    for k in range(len(te)):
+        fc, fw = st["flags"][k], st["flags"][k + len(te)]
+        if fc != D.INST_CONVERGED or fw != D.INST_CONVERGED:
+            rows.append(dict(k=k, cold=int(st["steps_to_tol"][k]), warm=int(st["steps_to_tol"][k + len(te)]),
+                             ok=False))
+            continue
+        cold, warm = steady_fields(b, k), steady_fields(b, k + len(te))
+        om_c, om_w = np.nan_to_num(cold["omega"]), np.nan_to_num(warm["omega"])
+        mask = np.isfinite(cold["omega"]) & np.isfinite(warm["omega"])
+        e_om = float(np.linalg.norm((om_w - om_c)[mask]) / np.linalg.norm(om_c[mask]))
+        tgt = targets(cold, te[k], n)
+        e_pred = float(np.linalg.norm(pred[k][..., :4] - tgt[..., :4]) / np.linalg.norm(tgt[..., :4]))
+        rows.append(dict(k=k, cold=int(st["steps_to_tol"][k]), warm=int(st["steps_to_tol"][k + len(te)]),
+                         ok=True, omega_rel_diff=e_om, pred_rel_err=e_pred, **te[k]))
+    good = [r for r in rows if r["ok"]]
+    cold_sum = sum(r["cold"] for r in good)
+    warm_sum = sum(r["warm"] for r in good)
+    ratios = [r["cold"] / max(r["warm"], 1) for r in good]
+    return dict(
+        grid=n, n_train=len(ok), n_train_drawn=len(tr), n_test=len(te), n_test_both_converged=len(good),
+        params=net.numel, epochs=epochs, final_loss=hist[-1] if hist else None,
+        steps_cold_total=cold_sum, steps_warm_total=warm_sum,
+        steps_saved_ratio=cold_sum / max(warm_sum, 1),
+        median_ratio=float(np.median(ratios)) if ratios else None,
+        omega_rel_diff_max=max((r["omega_rel_diff"] for r in good), default=None),
+        pred_rel_err_median=float(np.median([r["pred_rel_err"] for r in good])) if good else None,
+        seconds_data=t_data, seconds_train=t_train, rows=rows)
 
 
 def warm_start(pred, d, n):
