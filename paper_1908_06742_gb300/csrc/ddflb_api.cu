@@ -167,7 +167,23 @@ struct ddflb_ctx {
   float* stage;
   int64_t step;
   int64_t snap_step;  // step at which uprev was last written (-1: none)
+  int path;           // step kernel: 0 / 1 one node per thread, 2 paired nodes (16-bit storage)
 };
+
+namespace ddflb {
+// 16-bit storage, two adjacent nodes per thread (ddflb_step_pair.cu)
+bool pair_step_eligible(const Launch& L);
+cudaError_t launch_step_pair(const Launch& L, const void* fin, const void* gin, void* fout,
+                             void* gout, const DevStatus* st);
+}  // namespace ddflb
+
+namespace {
+cudaError_t run_step(const ddflb_ctx* c, const void* fin, const void* gin, void* fout, void* gout) {
+  if (c->path == 2 && pair_step_eligible(c->L))
+    return launch_step_pair(c->L, fin, gin, fout, gout, c->status);
+  return launch_step(c->L, fin, gin, fout, gout, c->status);
+}
+}  // namespace
 
 namespace {
 
@@ -305,7 +321,7 @@ ddflb_status ddflb_step(ddflb_ctx* c, int64_t n) {
     const int src = c->cur, dst = c->cur ^ 1;
     void* fo = c->pops[dst];
     void* go = (char*)fo + 9 * c->lay.pitch * (size_t)c->p.ny * elem_size(c->p.storage);
-    cudaError_t e = launch_step(c->L, fptr(c, src), gptr(c, src), fo, go, c->status);
+    cudaError_t e = run_step(c, fptr(c, src), gptr(c, src), fo, go);
     if (e != cudaSuccess) return cuda_fail(e, "step");
     c->cur = dst;
     ++c->step;
@@ -406,7 +422,7 @@ const char* ddflb_version(void) { return "ddflb 0.1 (sm_103a)"; }
 // fastest is kept.  The trials run on zeroed populations (the rest state), so
 // the state is overwritten and the step counter reset: call before ddflb_init.
 ddflb_status ddflb_autotune(ddflb_ctx* c, int32_t trial_steps, int32_t* block_x,
-                            int32_t* block_y, double* ms_per_step) {
+                            int32_t* block_y, int32_t* path, double* ms_per_step) {
   if (!c || trial_steps < 1) return fail(DDFLB_EINVAL, "NULL handle or trial_steps < 1");
   static const int shapes[][2] = {{128, 1}, {256, 1}, {64, 2}, {32, 4}, {64, 4}, {32, 8}, {64, 1}};
   cudaStream_t s = c->L.stream;
@@ -417,32 +433,41 @@ ddflb_status ddflb_autotune(ddflb_ctx* c, int32_t trial_steps, int32_t* block_x,
   cudaEventCreate(&e1);
   float best = 1e30f;
   dim3 bestb(128, 1, 1);
+  int bestp = 1;
+  const int saved_path = c->path;
   const size_t gofs = 9 * (size_t)c->lay.pitch * c->p.ny * elem_size(c->p.storage);
-  for (const auto& sh : shapes) {
-    c->L.block = dim3(sh[0], sh[1], 1);
-    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
-      if (rep == 1) e = cudaEventRecord(e0, s);
-      for (int i = 0; i < trial_steps && e == cudaSuccess; ++i) {
-        const int src = i & 1;
-        char* fo = (char*)c->pops[src ^ 1];
-        e = launch_step(c->L, c->pops[src], (const char*)c->pops[src] + gofs, fo, fo + gofs,
-                        c->status);
+  for (int pth = 1; pth <= 2 && e == cudaSuccess; ++pth) {
+    for (const auto& sh : shapes) {
+      c->L.block = dim3(sh[0], sh[1], 1);
+      c->path = pth;
+      if (pth == 2 && !pair_step_eligible(c->L)) continue;
+      for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+        if (rep == 1) e = cudaEventRecord(e0, s);
+        for (int i = 0; i < trial_steps && e == cudaSuccess; ++i) {
+          const int src = i & 1;
+          char* fo = (char*)c->pops[src ^ 1];
+          e = run_step(c, c->pops[src], (const char*)c->pops[src] + gofs, fo, fo + gofs);
+        }
       }
-    }
-    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
-    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-    float ms = 0.f;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-    if (e != cudaSuccess) break;
-    if (ms < best) {
-      best = ms;
-      bestb = c->L.block;
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) break;
+      if (ms < best) {
+        best = ms;
+        bestb = c->L.block;
+        bestp = pth;
+      }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  c->path = saved_path;
   if (e != cudaSuccess) return cuda_fail(e, "autotune trial");
   c->L.block = bestb;
+  c->path = bestp;
+  if (path) *path = bestp;
   e = cudaMemsetAsync(c->pops[0], 0, 2 * c->lay.pops_bytes, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "autotune reset");
@@ -454,6 +479,12 @@ ddflb_status ddflb_autotune(ddflb_ctx* c, int32_t trial_steps, int32_t* block_x,
   if (block_x) *block_x = (int32_t)bestb.x;
   if (block_y) *block_y = (int32_t)bestb.y;
   if (ms_per_step) *ms_per_step = best / trial_steps;
+  return DDFLB_OK;
+}
+
+ddflb_status ddflb_set_path(ddflb_ctx* c, int32_t path) {
+  if (!c || path < 0 || path > 2) return fail(DDFLB_EINVAL, "path must be 0, 1 or 2");
+  c->path = path;
   return DDFLB_OK;
 }
 

@@ -1,0 +1,195 @@
+// Fused step for 16-bit population storage, two adjacent nodes per thread.
+//
+// With FP16/BF16 storage a one-node-per-thread pull moves 2 bytes per memory
+// instruction, so the step is bound by instruction issue rather than by HBM.
+// Here each thread owns the pair of nodes (x0, x0 + 1), x0 even: every plane
+// is read as one aligned 4-byte pair; the populations pulled from x - 1 or
+// x + 1 come from the neighbouring lane's pair by a warp shuffle, with a
+// scalar load only at warp and row edges; stores are 4-byte pairs.  The
+// per-node arithmetic is exactly that of k_step (same device functions), so
+// results are bit-identical to the one-node kernel.
+//
+// Requirements: nx even, blockDim.x a multiple of 32 (a warp covers 64
+// consecutive nodes of one row).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "ddflb_device.cuh"
+#include "ddflb_internal.h"
+
+namespace ddflb {
+
+template <typename S> struct PairOf;
+template <> struct PairOf<__half> {
+  typedef __half2 T;
+  static __device__ __forceinline__ float lo(T v) { return __low2float(v); }
+  static __device__ __forceinline__ float hi(T v) { return __high2float(v); }
+  static __device__ __forceinline__ T pack(float a, float b) { return __floats2half2_rn(a, b); }
+  static __device__ __forceinline__ T zero() { return __floats2half2_rn(0.f, 0.f); }
+};
+template <> struct PairOf<__nv_bfloat16> {
+  typedef __nv_bfloat162 T;
+  static __device__ __forceinline__ float lo(T v) { return __low2float(v); }
+  static __device__ __forceinline__ float hi(T v) { return __high2float(v); }
+  static __device__ __forceinline__ T pack(float a, float b) { return __floats2bfloat162_rn(a, b); }
+  static __device__ __forceinline__ T zero() { return __floats2bfloat162_rn(0.f, 0.f); }
+};
+
+template <typename S>
+__device__ __forceinline__ typename PairOf<S>::T ld_pair(const S* p) {
+  typedef typename PairOf<S>::T T;
+  unsigned v = __ldg(reinterpret_cast<const unsigned*>(p));
+  return *reinterpret_cast<T*>(&v);
+}
+
+template <typename S>
+__device__ __forceinline__ void st_pair(S* p, float a, float b, float s) {
+  typedef typename PairOf<S>::T T;
+  T v = PairOf<S>::pack(a * s, b * s);
+  __stcs(reinterpret_cast<unsigned*>(p), *reinterpret_cast<unsigned*>(&v));
+}
+
+template <typename S, int BC>
+__global__ void __launch_bounds__(256) k_step_pair(LbParams P, const S* __restrict__ fin,
+                                                   const S* __restrict__ gin, S* __restrict__ fout,
+                                                   S* __restrict__ gout,
+                                                   const DevStatus* __restrict__ status) {
+  typedef PairOf<S> Q;
+  constexpr int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+  constexpr int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+  constexpr int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+  const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int lane = threadIdx.x & 31;
+  if (y >= P.ny) return;  // whole warps share y
+  if (status != nullptr && status->diverged) return;
+  const int nx = P.nx, ny = P.ny;
+  const int64_t pl = P.plane;
+  const bool live = x0 < nx;
+  int ym = y - 1, yp = y + 1;
+  bool sym = false, syp = false;
+  if (BC == BC_PERIODIC) {
+    if (ym < 0) ym += ny;
+    if (yp >= ny) yp -= ny;
+  } else {
+    sym = ym < 0;
+    syp = yp >= ny;
+  }
+  int xl = x0 - 1, xr = x0 + 2;  // left source of node A, right source of node B
+  bool sxl = false, sxr = false;
+  if (BC == BC_CAVITY) {
+    sxl = xl < 0;
+    sxr = xr >= nx;
+  } else {
+    if (xl < 0) xl += nx;
+    if (xr >= nx) xr -= nx;
+  }
+  const int64_t rows[3] = {(int64_t)ym * P.pitch, (int64_t)y * P.pitch, (int64_t)yp * P.pitch};
+  const int64_t own = (int64_t)y * P.pitch + x0;
+  float fA[9], fB[9], gA[9], gB[9];
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    const int ex = EX[a], ey = EY[a];
+    const bool ysolid = (ey == 1 && sym) || (ey == -1 && syp);
+    const int64_t ro = rows[1 - ey];
+    typename Q::T fp = Q::zero(), gp = Q::zero();
+    if (live && !ysolid) {
+      fp = ld_pair(fin + a * pl + ro + x0);
+      gp = ld_pair(gin + a * pl + ro + x0);
+    }
+    float fa, fb, ga, gb;
+    if (ex == 0) {
+      fa = Q::lo(fp); fb = Q::hi(fp); ga = Q::lo(gp); gb = Q::hi(gp);
+    } else if (ex == 1) {  // source x - 1: node A from the left lane, node B from own pair
+      float fl = __shfl_up_sync(0xffffffffu, Q::hi(fp), 1);
+      float gl = __shfl_up_sync(0xffffffffu, Q::hi(gp), 1);
+      if ((lane == 0 || x0 == 0) && live && !ysolid && !sxl) {
+        fl = Codec<S>::load(fin + a * pl + ro + xl, 1.0f);
+        gl = Codec<S>::load(gin + a * pl + ro + xl, 1.0f);
+      }
+      fa = fl; fb = Q::lo(fp); ga = gl; gb = Q::lo(gp);
+    } else {  // source x + 1: node A from own pair, node B from the right lane
+      float fr = __shfl_down_sync(0xffffffffu, Q::lo(fp), 1);
+      float gr = __shfl_down_sync(0xffffffffu, Q::lo(gp), 1);
+      if ((lane == 31 || x0 + 2 >= nx) && live && !ysolid && !sxr) {
+        fr = Codec<S>::load(fin + a * pl + ro + xr, 1.0f);
+        gr = Codec<S>::load(gin + a * pl + ro + xr, 1.0f);
+      }
+      fa = Q::hi(fp); fb = fr; ga = Q::hi(gp); gb = gr;
+    }
+    fA[a] = fa * P.isf; fB[a] = fb * P.isf; gA[a] = ga * P.isg; gB[a] = gb * P.isg;
+    if (BC != BC_PERIODIC) {
+      // half-way bounce-back: the node's own post-collision value of the
+      // opposite direction, with the moving-wall / fixed-scalar terms
+      const bool solA = ysolid || (ex == 1 && sxl);
+      const bool solB = ysolid || (ex == -1 && sxr);
+      if ((solA || solB) && live) {
+        const typename Q::T fo = ld_pair(fin + OPP[a] * pl + own);
+        const typename Q::T go = ld_pair(gin + OPP[a] * pl + own);
+        const bool lid = ey == -1 && syp;
+        const float lf = lid ? P.lid[a] : 0.0f;
+        const float lg = lid ? P.abb_lid[a] : P.abb_wall[a];
+        if (solA) {
+          fA[a] = Q::lo(fo) * P.isf + lf;
+          gA[a] = lg - Q::lo(go) * P.isg;
+        }
+        if (solB) {
+          fB[a] = Q::hi(fo) * P.isf + lf;
+          gB[a] = lg - Q::hi(go) * P.isg;
+        }
+      }
+    }
+  }
+  if (!live) return;
+  {
+    const Mom mf = moments_flow(fA), mg = moments_scalar(gA);
+    const Macro q = macro(P, mf, mg);
+    relax(P.wf, neq_flow(mf, q), fA);
+    relax(P.wg, neq_scalar(P, mg, mf, q), gA);
+  }
+  {
+    const Mom mf = moments_flow(fB), mg = moments_scalar(gB);
+    const Macro q = macro(P, mf, mg);
+    relax(P.wf, neq_flow(mf, q), fB);
+    relax(P.wg, neq_scalar(P, mg, mf, q), gB);
+  }
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    st_pair(fout + a * pl + own, fA[a], fB[a], P.sf);
+    st_pair(gout + a * pl + own, gA[a], gB[a], P.sg);
+  }
+}
+
+namespace {
+template <typename S, int BC>
+cudaError_t go(const Launch& L, const void* fin, const void* gin, void* fout, void* gout,
+               const DevStatus* st) {
+  const dim3 b = L.block;
+  const dim3 g((L.P.nx / 2 + b.x - 1) / b.x, (L.P.ny + b.y - 1) / b.y);
+  k_step_pair<S, BC><<<g, b, 0, L.stream>>>(L.P, (const S*)fin, (const S*)gin, (S*)fout,
+                                            (S*)gout, st);
+  return cudaGetLastError();
+}
+template <typename S>
+cudaError_t go_bc(const Launch& L, const void* fin, const void* gin, void* fout, void* gout,
+                  const DevStatus* st) {
+  switch (L.P_bc) {
+    case BC_PERIODIC: return go<S, BC_PERIODIC>(L, fin, gin, fout, gout, st);
+    case BC_CAVITY: return go<S, BC_CAVITY>(L, fin, gin, fout, gout, st);
+    default: return go<S, BC_CHANNEL>(L, fin, gin, fout, gout, st);
+  }
+}
+}  // namespace
+
+bool pair_step_eligible(const Launch& L) {
+  return L.storage != 0 && L.P.nx % 2 == 0 && L.block.x % 32 == 0;
+}
+
+cudaError_t launch_step_pair(const Launch& L, const void* fin, const void* gin, void* fout,
+                             void* gout, const DevStatus* st) {
+  if (L.storage == 1) return go_bc<__half>(L, fin, gin, fout, gout, st);
+  return go_bc<__nv_bfloat16>(L, fin, gin, fout, gout, st);
+}
+
+}  // namespace ddflb

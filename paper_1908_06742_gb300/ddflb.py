@@ -86,7 +86,8 @@ SIGNATURES = {
     "ddflb_batch_debug_skip_barrier": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "ddflb_batch_autotune": (ctypes.c_int, [_VP, ctypes.c_int32] +
                              [ctypes.POINTER(ctypes.c_int32)] * 3 + [ctypes.POINTER(ctypes.c_double)]),
-    "ddflb_autotune": (ctypes.c_int, [_VP, ctypes.c_int32] + [ctypes.POINTER(ctypes.c_int32)] * 2 +
+    "ddflb_set_path": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "ddflb_autotune": (ctypes.c_int, [_VP, ctypes.c_int32] + [ctypes.POINTER(ctypes.c_int32)] * 3 +
                        [ctypes.POINTER(ctypes.c_double)]),
     "ddflb_set_block": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32]),
     # warm-start surrogate network kernels
@@ -311,15 +312,21 @@ class Lattice:
         key = tuning.key("lattice", [self.cfg])
         hit = tuning.lookup(key) if cache else None
         if hit:
-            _check(self.lib.ddflb_set_block(self._h, *hit["choice"]))
+            _check(self.lib.ddflb_set_block(self._h, *hit["choice"][:2]))
+            _check(self.lib.ddflb_set_path(self._h, hit["choice"][2]))
             return hit
-        bx, by, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+        bx, by, pth, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
         _check(self.lib.ddflb_autotune(self._h, int(trial_steps), ctypes.byref(bx),
-                                       ctypes.byref(by), ctypes.byref(ms)))
-        rec = {"choice": [bx.value, by.value], "ms_per_step": ms.value}
+                                       ctypes.byref(by), ctypes.byref(pth), ctypes.byref(ms)))
+        rec = {"choice": [bx.value, by.value, pth.value], "ms_per_step": ms.value}
         if cache:
             tuning.store(key, rec)
         return rec
+
+    def set_path(self, path: int):
+        """Step kernel variant: 0 automatic, 1 one node per thread, 2 paired nodes."""
+        _check(self.lib.ddflb_set_path(self._h, int(path)))
+        return self
 
     def state_bytes(self) -> int:
         return self.lib.ddflb_state_bytes(self._h)
