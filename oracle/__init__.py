@@ -49,6 +49,7 @@ class _Params(ctypes.Structure):
         ("u_lid", ctypes.c_double), ("phi_lid", ctypes.c_double), ("phi_wall", ctypes.c_double),
         ("phi_min", ctypes.c_double),
         ("scale_f", ctypes.c_double), ("scale_g", ctypes.c_double),
+        ("fx", ctypes.c_double), ("fy", ctypes.c_double), ("f_omega", ctypes.c_double),
     ]
 
 
@@ -65,10 +66,11 @@ def lib():
         L.orc_equilibria.argtypes = [ctypes.POINTER(_Params), ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_double, _D, _D]
         L.orc_collide_node.argtypes = [ctypes.POINTER(_Params), _D, _D, _D, _D]
-        L.orc_init.argtypes = [ctypes.POINTER(_Params), _D, _D, _D, _D, _D, _D, _D]
-        L.orc_step.argtypes = [ctypes.POINTER(_Params), _D, _D, _D, _D, ctypes.c_int64]
-        L.orc_fields.argtypes = [ctypes.POINTER(_Params), _D, _D, _D, _D]
-        L.orc_sums.argtypes = [ctypes.POINTER(_Params), _D, _D, _D]
+        L.orc_init.argtypes = [ctypes.POINTER(_Params), _D, _D, _D, _D, _D, _D, _D, _D]
+        L.orc_step.argtypes = [ctypes.POINTER(_Params), _D, _D, _D, _D, ctypes.c_int64, _D,
+                               ctypes.c_int64]
+        L.orc_fields.argtypes = [ctypes.POINTER(_Params), _D, _D, _D, _D, _D, ctypes.c_int64]
+        L.orc_sums.argtypes = [ctypes.POINTER(_Params), _D, _D, _D, _D, ctypes.c_int64]
         L.orc_round.argtypes = [ctypes.c_int32, _D, ctypes.c_int64]
         L.orc_threads.argtypes = [ctypes.c_int]
         L.orc_threads.restype = ctypes.c_int
@@ -112,6 +114,9 @@ class OracleParams:
     storage: str = "fp64"
     scale_f: float = 1.0
     scale_g: float = 1.0
+    fx: float = 0.0                # constant body force (Sec. 2)
+    fy: float = 0.0
+    f_omega: float = 0.0           # force modulation cos(f_omega t), 0 = steady
     lam_override: Optional[tuple] = None      # full 9-entry flow diagonal (tests)
     lam_phi_override: Optional[tuple] = None  # full 9-entry scalar diagonal (tests)
 
@@ -142,6 +147,7 @@ class OracleParams:
         p.u_lid, p.phi_lid, p.phi_wall = self.u_lid, self.phi_lid, self.phi_wall
         p.phi_min = self.phi_min
         p.scale_f, p.scale_g = self.scale_f, self.scale_g
+        p.fx, p.fy, p.f_omega = self.fx, self.fy, self.f_omega
         return p
 
 
@@ -194,14 +200,21 @@ class OracleLattice:
         shape = (Q, params.ny, params.nx)
         self.f = np.zeros(shape); self.g = np.zeros(shape)
         self._fs = np.zeros(shape); self._gs = np.zeros(shape)
+        self.force = None   # optional body-force field [2, ny, nx] added to (fx, fy)
         self.t = 0
+
+    def set_force(self, field):
+        """Spatially varying body force (Fx, Fy) per node, [2, ny, nx]."""
+        self.force = None if field is None else np.ascontiguousarray(field, np.float64).reshape(
+            2, self.p.ny, self.p.nx)
+        return self
 
     def init(self, rho, ux, uy, phi, grads=None):
         c = lambda a: np.ascontiguousarray(np.broadcast_to(a, (self.p.ny, self.p.nx)), np.float64)
         rho, ux, uy, phi = c(rho), c(ux), c(uy), c(phi)
         gr = None if grads is None else np.ascontiguousarray(grads, np.float64).reshape(6, self.p.ny, self.p.nx)
         lib().orc_init(ctypes.byref(self._cp), _ptr(rho), _ptr(ux), _ptr(uy), _ptr(phi), _ptr(gr),
-                       _ptr(self.f), _ptr(self.g))
+                       _ptr(self.f), _ptr(self.g), _ptr(self.force))
         self.t = 0
         return self
 
@@ -211,7 +224,7 @@ class OracleLattice:
 
     def step(self, n: int = 1):
         lib().orc_step(ctypes.byref(self._cp), _ptr(self.f), _ptr(self.g), _ptr(self._fs),
-                       _ptr(self._gs), int(n))
+                       _ptr(self._gs), int(n), _ptr(self.force), int(self.t))
         self.t += n
         return self
 
@@ -219,7 +232,8 @@ class OracleLattice:
         ny, nx = self.p.ny, self.p.nx
         out = np.zeros((8, ny, nx))
         ex = np.zeros((8, ny, nx)) if extra else None
-        lib().orc_fields(ctypes.byref(self._cp), _ptr(self.f), _ptr(self.g), _ptr(out), _ptr(ex))
+        lib().orc_fields(ctypes.byref(self._cp), _ptr(self.f), _ptr(self.g), _ptr(out), _ptr(ex),
+                         _ptr(self.force), int(self.t))
         d = {k: out[i] for i, k in enumerate(FIELD_NAMES)}
         if extra:
             d.update({k: ex[i] for i, k in enumerate(EXTRA_NAMES)})
@@ -227,5 +241,6 @@ class OracleLattice:
 
     def sums(self):
         out = np.zeros(3)
-        lib().orc_sums(ctypes.byref(self._cp), _ptr(self.f), _ptr(self.g), _ptr(out))
+        lib().orc_sums(ctypes.byref(self._cp), _ptr(self.f), _ptr(self.g), _ptr(out),
+                       _ptr(self.force), int(self.t))
         return {"mass": out[0], "scalar": out[1], "u2": out[2]}

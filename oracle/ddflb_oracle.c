@@ -40,6 +40,8 @@ typedef struct {
   double u_lid, phi_lid, phi_wall;
   double phi_min;               /* |phi| below this: cross derivatives and vorticity are NaN */
   double scale_f, scale_g;      /* storage scale for the rounding emulation */
+  double fx, fy;                /* constant body force (Sec. 2, F in Eq. momentumeqn) */
+  double f_omega;               /* force modulation cos(f_omega t); 0 = steady */
 } orc_params;
 
 /* ---------------------------------------------------------------------------
@@ -179,16 +181,38 @@ static double emulate(const orc_params* p, double v, double wref, double scale) 
  * F = 0); phi = sum g; relax in moment space; back to velocity space by T^-1
  * (Eqs. MRT-LBEfluidmotion_transformed, MRT-LBECDE).
  * ------------------------------------------------------------------------- */
+/* Source moments of the body force F = (Fx, Fy) at velocity u (Sec. 2, the
+ * moments sigma' listed after Eq. eqmrawmoment), arranged like m. */
+static void source_m(double Fx, double Fy, double ux, double uy, double* S) {
+  raw_to_m(0.0, Fx, Fy, 2.0 * Fx * ux, 2.0 * Fy * uy, Fx * uy + Fy * ux,
+           Fy * ux * ux + 2.0 * Fx * ux * uy, Fx * uy * uy + 2.0 * Fy * uy * ux,
+           2.0 * (Fx * ux * uy * uy + Fy * uy * ux * ux), S);
+}
+
+/* Force acting at node c at time t: constant part plus optional field, times
+ * cos(f_omega t) when f_omega != 0 (pulsatile driving, Sec. 5.3). */
+static void node_force(const orc_params* p, const double* field, size_t N, size_t c, int64_t t,
+                       double* Fx, double* Fy) {
+  const double mod = p->f_omega != 0.0 ? cos(p->f_omega * (double)t) : 1.0;
+  *Fx = (p->fx + (field ? field[c] : 0.0)) * mod;
+  *Fy = (p->fy + (field ? field[N + c] : 0.0)) * mod;
+}
+
+/* The populations held are f-bar = f - S/2 (the transformation that makes the
+ * trapezoidal source explicit, Sec. 2), so u = (sum f-bar e + F/2) / rho
+ * (Eq. hydrodynamic_fields) and the collision of Eq.
+ * MRT-LBEfluidmotion_transformed is m* = m - Lambda (m - m^eq) + (I - Lambda/2) S. */
 static void collide_node(const orc_params* p, const double* f, const double* g,
-                         double* fs, double* gs) {
-  double m[Q], n[Q], meq[Q], neq[Q], ms[Q], ns[Q];
+                         double* fs, double* gs, double Fx, double Fy) {
+  double m[Q], n[Q], meq[Q], neq[Q], ms[Q], ns[Q], S[Q];
   matvec(T_, f, m);
   matvec(T_, g, n);
-  double rho = m[0], ux = m[1] / rho, uy = m[2] / rho, phi = n[0];
+  double rho = m[0], ux = (m[1] + 0.5 * Fx) / rho, uy = (m[2] + 0.5 * Fy) / rho, phi = n[0];
   eq_flow(rho, ux, uy, p->cs2, meq);
   eq_scalar(phi, ux, uy, p->cs2_phi, p->beta1, p->beta2, neq);
+  source_m(Fx, Fy, ux, uy, S);
   for (int k = 0; k < Q; ++k) {
-    ms[k] = m[k] - p->lam[k] * (m[k] - meq[k]);
+    ms[k] = m[k] - p->lam[k] * (m[k] - meq[k]) + (1.0 - 0.5 * p->lam[k]) * S[k];
     ns[k] = n[k] - p->lam_phi[k] * (n[k] - neq[k]);
   }
   matvec(TI_, ms, fs);
@@ -208,7 +232,8 @@ static int opposite(int a) {
  * with u_w = (u_lid, 0), phi_w = phi_lid when the upstream node is above the
  * top row, else u_w = 0, phi_w = phi_wall (Sec. 5: half-way bounce-back,
  * moving-lid momentum term, fixed scalar value on the walls). */
-static void step_once(const orc_params* p, double* f, double* g, double* fs, double* gs) {
+static void step_once(const orc_params* p, double* f, double* g, double* fs, double* gs,
+                      const double* force, int64_t t) {
   const int nx = p->nx, ny = p->ny;
   const size_t N = (size_t)nx * ny;
   double w[Q], wp[Q];
@@ -218,9 +243,10 @@ static void step_once(const orc_params* p, double* f, double* g, double* fs, dou
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i) {
       size_t c = (size_t)j * nx + i;
-      double fl[Q], gl[Q], fo[Q], go[Q];
+      double fl[Q], gl[Q], fo[Q], go[Q], Fx, Fy;
       for (int a = 0; a < Q; ++a) { fl[a] = f[a * N + c]; gl[a] = g[a * N + c]; }
-      collide_node(p, fl, gl, fo, go);
+      node_force(p, force, N, c, t, &Fx, &Fy);
+      collide_node(p, fl, gl, fo, go, Fx, Fy);
       for (int a = 0; a < Q; ++a) {
         fs[a * N + c] = emulate(p, fo[a], w[a] * p->rho0, p->scale_f);
         gs[a * N + c] = emulate(p, go[a], wp[a] * p->phi0, p->scale_g);
@@ -279,7 +305,7 @@ void orc_equilibria(const orc_params* p, double rho, double ux, double uy, doubl
 void orc_collide_node(const orc_params* p, const double* f, const double* g, double* fs,
                       double* gs) {
   ensure_basis();
-  collide_node(p, f, g, fs, gs);
+  collide_node(p, f, g, fs, gs, 0.0, 0.0);
 }
 
 /* Initial populations from macroscopic fields.
@@ -288,9 +314,11 @@ void orc_collide_node(const orc_params* p, const double* f, const double* g, dou
  * and Eqs. (1stnoneqmmomentx_CDE), (1stnoneqmmomenty_CDE),
  * (offdiagonal2ndnoneqmmoment_CDE) for the scalar; all other non-equilibrium
  * moments are zero.  grads = 6 planes (dxux, dyux, dxuy, dyuy, dxphi, dyphi) or
- * NULL for the pure equilibrium. */
+ * NULL for the pure equilibrium.  With a body force the flow populations held
+ * are f-bar = f - S/2 (force at t = 0). */
 void orc_init(const orc_params* p, const double* rho, const double* ux, const double* uy,
-              const double* phi, const double* grads, double* f, double* g) {
+              const double* phi, const double* grads, double* f, double* g,
+              const double* force) {
   ensure_basis();
   const size_t N = (size_t)p->nx * p->ny;
   const double cs2 = p->cs2, cp2 = p->cs2_phi;
@@ -299,9 +327,12 @@ void orc_init(const orc_params* p, const double* rho, const double* ux, const do
   rest_weights(p->cs2_phi, wp);
 #pragma omp parallel for schedule(static)
   for (long c = 0; c < (long)N; ++c) {
-    double m[Q], n[Q], fl[Q], gl[Q];
+    double m[Q], n[Q], fl[Q], gl[Q], S[Q], Fx, Fy;
     double r = rho[c], vx = ux[c], vy = uy[c], ph = phi[c];
     eq_flow(r, vx, vy, cs2, m);
+    node_force(p, force, N, (size_t)c, 0, &Fx, &Fy);
+    source_m(Fx, Fy, vx, vy, S);
+    for (int k = 0; k < Q; ++k) m[k] -= 0.5 * S[k];
     eq_scalar(ph, vx, vy, cp2, p->beta1, p->beta2, n);
     if (grads) {
       double dxux = grads[0 * N + c], dyux = grads[1 * N + c];
@@ -328,9 +359,9 @@ void orc_init(const orc_params* p, const double* rho, const double* ux, const do
 /* Advance nsteps; f, g hold the pre-collision state on entry and exit.
  * fs, gs are caller scratch of the same size. */
 void orc_step(const orc_params* p, double* f, double* g, double* fs, double* gs,
-              int64_t nsteps) {
+              int64_t nsteps, const double* force, int64_t t0) {
   ensure_basis();
-  for (int64_t t = 0; t < nsteps; ++t) step_once(p, f, g, fs, gs);
+  for (int64_t t = t0; t < t0 + nsteps; ++t) step_once(p, f, g, fs, gs, force, t);
 }
 
 /* Local kinematics from the current (pre-collision) populations, Sec. 4:
@@ -338,17 +369,22 @@ void orc_step(const orc_params* p, double* f, double* g, double* fs, double* gs,
  * receives 6 more planes (dxux, dyux, dxuy, dyuy, N_xy, N^phi_xy) and, after
  * them, (dxphi, dyphi). */
 void orc_fields(const orc_params* p, const double* f, const double* g, double* out,
-                double* extra) {
+                double* extra, const double* force, int64_t t) {
   ensure_basis();
   const size_t N = (size_t)p->nx * p->ny;
   const double cs2 = p->cs2, cp2 = p->cs2_phi, b1 = p->beta1, b2 = p->beta2;
 #pragma omp parallel for schedule(static)
   for (long c = 0; c < (long)N; ++c) {
-    double fl[Q], gl[Q], m[Q], n[Q];
+    double fl[Q], gl[Q], m[Q], n[Q], S[Q], Fx, Fy;
     for (int a = 0; a < Q; ++a) { fl[a] = f[a * N + c]; gl[a] = g[a * N + c]; }
     matvec(T_, fl, m);
     matvec(T_, gl, n);
-    double rho = m[0], ux = m[1] / rho, uy = m[2] / rho, phi = n[0];
+    node_force(p, force, N, (size_t)c, t, &Fx, &Fy);
+    double rho = m[0], ux = (m[1] + 0.5 * Fx) / rho, uy = (m[2] + 0.5 * Fy) / rho, phi = n[0];
+    /* moments of f = f-bar + S/2 (reading: the non-equilibrium moments of Sec. 4
+     * are those of the distribution f itself) */
+    source_m(Fx, Fy, ux, uy, S);
+    for (int k = 3; k < Q; ++k) m[k] += 0.5 * S[k];
     /* non-equilibrium moments, Sec. 4 (local evaluation) */
     double m3 = m[3] - (2.0 * cs2 * rho + rho * (ux * ux + uy * uy));
     double m4 = m[4] - rho * (ux * ux - uy * uy);
@@ -393,7 +429,8 @@ void orc_fields(const orc_params* p, const double* f, const double* g, double* o
 
 /* Global sums over the pre-collision state: (sum rho, sum phi, sum |u|^2).
  * Row sums in parallel, then rows added in order (deterministic). */
-void orc_sums(const orc_params* p, const double* f, const double* g, double* out3) {
+void orc_sums(const orc_params* p, const double* f, const double* g, double* out3,
+              const double* force, int64_t t) {
   ensure_basis();
   const int nx = p->nx, ny = p->ny;
   const size_t N = (size_t)nx * ny;
@@ -403,11 +440,12 @@ void orc_sums(const orc_params* p, const double* f, const double* g, double* out
     double sr = 0, sp = 0, su = 0;
     for (int i = 0; i < nx; ++i) {
       size_t c = (size_t)j * nx + i;
-      double fl[Q], gl[Q], m[Q], n[Q];
+      double fl[Q], gl[Q], m[Q], n[Q], Fx, Fy;
       for (int a = 0; a < Q; ++a) { fl[a] = f[a * N + c]; gl[a] = g[a * N + c]; }
       matvec(T_, fl, m);
       matvec(T_, gl, n);
-      double ux = m[1] / m[0], uy = m[2] / m[0];
+      node_force(p, force, N, c, t, &Fx, &Fy);
+      double ux = (m[1] + 0.5 * Fx) / m[0], uy = (m[2] + 0.5 * Fy) / m[0];
       sr += m[0];
       sp += n[0];
       su += ux * ux + uy * uy;

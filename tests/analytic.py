@@ -47,5 +47,42 @@ def laplace_lid(n, terms=401):
     return phi
 
 
+def poiseuille(H, F, nu, rho=1.0):
+    """Steady plane Poiseuille flow between half-way walls at y = -1/2 and
+    H - 1/2 driven by a body force F: u_x(j), and omega_z = -d u_x / dy."""
+    y = np.arange(H) + 0.5
+    ux = F / (2 * rho * nu) * y * (H - y)
+    om = -F / (2 * rho * nu) * (H - 2 * y)
+    return ux, om
+
+
+def four_rolls(n, u0, nu, rho=1.0):
+    """Steady four-rolls mill on a periodic n x n grid (k = 2 pi / n): the body
+    force F = 2 rho nu k^2 u0 (sin kx sin ky, cos kx cos ky) sustains
+    u = u0 (sin kx sin ky, cos kx cos ky), omega = -2 u0 k sin kx cos ky."""
+    k = 2 * math.pi / n
+    x = np.arange(n)[None, :].astype(float)
+    y = np.arange(n)[:, None].astype(float)
+    sx, cx, sy, cy = np.sin(k * x), np.cos(k * x), np.sin(k * y), np.cos(k * y)
+    ux, uy = u0 * sx * sy, u0 * cx * cy
+    force = np.stack([2 * rho * nu * k * k * ux, 2 * rho * nu * k * k * uy])
+    return dict(ux=ux, uy=uy, omega=-2 * u0 * k * sx * cy, force=force)
+
+
+def womersley(H, Fm, Omega, nu, t, rho=1.0):
+    """Channel flow driven by F_x = Fm cos(Omega t) between walls at distance
+    H (half-way walls): u = Re{ Fm/(i Omega rho) [1 - cosh(kappa eta)/cosh(kappa L)] e^{i Omega t} },
+    kappa = sqrt(i Omega / nu), eta the distance from the centre line, L = H/2;
+    omega_z = -du/dy."""
+    eta = np.arange(H) + 0.5 - H / 2
+    L = H / 2
+    kap = np.sqrt(1j * Omega / nu)
+    amp = Fm / (1j * Omega * rho)
+    e = np.exp(1j * Omega * t)
+    u = np.real(amp * (1 - np.cosh(kap * eta) / np.cosh(kap * L)) * e)
+    om = np.real(amp * kap * np.sinh(kap * eta) / np.cosh(kap * L) * e)
+    return u, om
+
+
 def rel_l2(a, b):
     return float(np.sqrt(np.sum((a - b) ** 2) / np.sum(b ** 2)))
