@@ -6,7 +6,7 @@
  * distribution functions based lattice Boltzmann methods for flow and scalar
  * transport", arXiv 1908.06742.  Two D2Q9 lattices advance together: the flow
  * populations f with the MRT collision of Sec. 2 (Eq. MRT-LBEfluidmotion_transformed,
- * body force F = 0) and the passive-scalar populations g with the MRT collision
+ * optional body force) and the passive-scalar populations g with the MRT collision
  * of Sec. 3 (Eq. MRT-LBECDE), whose third-order off-diagonal equilibria carry
  * the anisotropy beta1 != beta2 (Eq. eqmrawmoment_CDE).  The strain rate S_ij
  * and the vorticity omega_z are recovered node by node from the second-order
@@ -91,6 +91,16 @@ typedef struct {
   double scale_f, scale_g; /* storage scale (power of two; <= 0 means 1)           */
   int32_t check_every;  /* steps between reductions in ddflb_step (0 = none)        */
   int32_t flags;        /* DDFLB_FLAG_*                                             */
+  /* Body force F in the momentum equation (Sec. 2), acting at node x at time t:
+   *   F(x, t) = (fx + field_x(x), fy + field_y(x)) cos(force_omega t)
+   * (force_omega = 0: steady; field from ddflb_set_force_field, zero without).
+   * With a force the flow populations held are f-bar = f - S/2, S the source of
+   * Eq. (MRT-LBEfluidmotion_transformed) whose moments are the sigma' listed
+   * after Eq. (eqmrawmoment); u = (sum_a f-bar_a e_a + F/2) / rho (Eq.
+   * hydrodynamic_fields); ddflb_populations returns f-bar.  The batched entry
+   * points and ddflb_reduce_noalloc accept only fx = fy = force_omega = 0. */
+  double fx, fy;
+  double force_omega;
 } ddflb_params;
 
 typedef struct ddflb_ctx ddflb_ctx;
@@ -207,6 +217,15 @@ ddflb_status ddflb_set_block(ddflb_ctx* c, int32_t block_x, int32_t block_y);
  * Both give bit-identical results; which is faster depends on the shape, so
  * the autotuner times both. */
 ddflb_status ddflb_set_path(ddflb_ctx* c, int32_t path);
+
+/* Spatially varying part of the body force (Sec. 2; e.g. the four-rolls mill
+ * of Sec. 5.2): dev_field is a device array [2][ny][nx] of floats (F_x plane,
+ * then F_y), added to (fx, fy) of the parameters and modulated with them by
+ * cos(force_omega t).  The caller owns the array and keeps it alive and
+ * unchanged while the context steps; NULL removes the field.  Takes effect for
+ * the next ddflb_init, ddflb_step, ddflb_fields and ddflb_stats.  A forced
+ * context always runs the one-node-per-thread step kernel. */
+ddflb_status ddflb_set_force_field(ddflb_ctx* c, const float* dev_field);
 
 /* Release the handle (host memory only; the workspace stays the caller's). */
 ddflb_status ddflb_destroy(ddflb_ctx* c);

@@ -94,6 +94,8 @@ ddflb_status validate(const ddflb_params* p) {
       !std::isfinite(p->phi_wall) || !(p->phi_min >= 0))
     return fail(DDFLB_EINVAL, "non-finite boundary or reference value");
   if (p->check_every < 0) return fail(DDFLB_EINVAL, "check_every < 0");
+  if (!std::isfinite(p->fx) || !std::isfinite(p->fy) || !std::isfinite(p->force_omega))
+    return fail(DDFLB_EINVAL, "non-finite body force or force frequency");
   for (double s : {p->scale_f, p->scale_g}) {
     if (s > 0) {
       int e;
@@ -144,6 +146,10 @@ LbParams make_lb(const ddflb_params* p, int pitch) {
     P.abb_lid[a] = (float)(2.0 * wg * (p->phi_lid - p->phi0));
     P.abb_wall[a] = (float)(2.0 * wg * (p->phi_wall - p->phi0));
   }
+  P.fx = (float)p->fx;
+  P.fy = (float)p->fy;
+  P.fmod = 1.0f;
+  P.ffield = nullptr;
   return P;
 }
 
@@ -169,6 +175,18 @@ struct ddflb_ctx {
   int64_t snap_step;  // step at which uprev was last written (-1: none)
   int path;           // step kernel: 0 / 1 one node per thread, 2 paired nodes (16-bit storage)
 };
+
+namespace {
+// Body-force modulation cos(force_omega t) for the launches that act on the
+// state at time t (the collision of step t, and fields / sums of state t).
+void at_time(ddflb_ctx* c, int64_t t) {
+  c->L.P.fmod = c->p.force_omega != 0.0 ? (float)std::cos(c->p.force_omega * (double)t) : 1.0f;
+}
+
+bool has_force(const ddflb_params& p, const float* field) {
+  return p.fx != 0.0 || p.fy != 0.0 || field != nullptr;
+}
+}  // namespace
 
 namespace ddflb {
 // 16-bit storage, two adjacent nodes per thread (ddflb_step_pair.cu)
@@ -204,6 +222,7 @@ ddflb_status check_launch(cudaError_t e, const char* where) {
 }
 
 ddflb_status reduce(ddflb_ctx* c, int mode) {
+  at_time(c, c->step);
   cudaError_t e = launch_reduce(c->L, fptr(c, c->cur), gptr(c, c->cur), c->uprev, mode,
                                 c->partials, c->status);
   if (e != cudaSuccess) return cuda_fail(e, "reduce");
@@ -258,6 +277,7 @@ ddflb_status ddflb_create(const ddflb_params* p, void* ws, size_t bytes, void* s
   c->L.P = make_lb(p, lay.pitch);
   c->L.P_bc = p->bc;
   c->L.storage = p->storage;
+  c->L.force = has_force(*p, nullptr);
   c->L.block = dim3(128, 1, 1);
   c->L.stream = (cudaStream_t)stream;
   c->step = 0;
@@ -286,6 +306,7 @@ ddflb_status ddflb_init(ddflb_ctx* c, const float* rho, const float* ux, const f
   c->cur = 0;
   c->step = 0;
   c->snap_step = -1;
+  at_time(c, 0);
   InitPtrs in{rho, ux, uy, phi, grads};
   void* f = c->pops[0];
   void* g = (char*)f + 9 * c->lay.pitch * (size_t)c->p.ny * elem_size(c->p.storage);
@@ -321,6 +342,7 @@ ddflb_status ddflb_step(ddflb_ctx* c, int64_t n) {
     const int src = c->cur, dst = c->cur ^ 1;
     void* fo = c->pops[dst];
     void* go = (char*)fo + 9 * c->lay.pitch * (size_t)c->p.ny * elem_size(c->p.storage);
+    at_time(c, c->step);
     cudaError_t e = run_step(c, fptr(c, src), gptr(c, src), fo, go);
     if (e != cudaSuccess) return cuda_fail(e, "step");
     c->cur = dst;
@@ -335,6 +357,7 @@ ddflb_status ddflb_fields(ddflb_ctx* c, float* rho, float* ux, float* uy, float*
                           float* sxy, float* syy, float* omega) {
   if (!c) return fail(DDFLB_EINVAL, "NULL handle");
   FieldPtrs fp{{rho, ux, uy, phi, sxx, sxy, syy, omega}};
+  at_time(c, c->step);
   return check_launch(launch_fields(c->L, fptr(c, c->cur), gptr(c, c->cur), fp), "fields");
 }
 
@@ -346,6 +369,7 @@ ddflb_status ddflb_fields_host(ddflb_ctx* c, float* rho, float* ux, float* uy, f
   float* host[8] = {rho, ux, uy, phi, sxx, sxy, syy, omega};
   FieldPtrs fp{};
   for (int k = 0; k < 8; ++k) fp.p[k] = host[k] ? c->stage + k * n : nullptr;
+  at_time(c, c->step);
   ddflb_status s =
       check_launch(launch_fields(c->L, fptr(c, c->cur), gptr(c, c->cur), fp), "fields_host");
   if (s != DDFLB_OK) return s;
@@ -488,6 +512,13 @@ ddflb_status ddflb_set_path(ddflb_ctx* c, int32_t path) {
   return DDFLB_OK;
 }
 
+ddflb_status ddflb_set_force_field(ddflb_ctx* c, const float* dev_field) {
+  if (!c) return fail(DDFLB_EINVAL, "NULL handle");
+  c->L.P.ffield = dev_field;
+  c->L.force = has_force(c->p, dev_field);
+  return DDFLB_OK;
+}
+
 ddflb_status ddflb_set_block(ddflb_ctx* c, int32_t block_x, int32_t block_y) {
   if (!c) return fail(DDFLB_EINVAL, "NULL handle");
   if (block_x < 32 || block_y < 1 || block_x % 32 || block_x * block_y > 256 ||
@@ -544,6 +575,8 @@ extern "C" ddflb_status ddflb_reduce_noalloc(const ddflb_params* p, const void* 
   if (s != DDFLB_OK) return s;
   if (!dev_state || !dev_out) return fail(DDFLB_EINVAL, "NULL state or output");
   if (mode < 0 || mode > 3) return fail(DDFLB_EINVAL, "mode %d not in 0..3", mode);
+  if (p->fx != 0.0 || p->fy != 0.0 || p->force_omega != 0.0)
+    return fail(DDFLB_EINVAL, "ddflb_reduce_noalloc takes unforced states only");
   const int64_t nodes = (int64_t)p->nx * p->ny;
   if (nodes > DDFLB_NOALLOC_MAX_NODES)
     return fail(DDFLB_EINVAL,
@@ -579,6 +612,7 @@ extern "C" ddflb_status ddflb_reduce_noalloc(const ddflb_params* p, const void* 
   L.P = make_lb(p, lay.pitch);
   L.P_bc = p->bc;
   L.storage = p->storage;
+  L.force = false;
   L.block = dim3(128, 1, 1);
   L.stream = st;
   // the status block keeps the last call's contents: clear it (diverged flag, residual)

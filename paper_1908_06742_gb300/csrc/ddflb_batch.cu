@@ -498,6 +498,10 @@ size_t ddflb_batch_workspace_bytes(int32_t n, const ddflb_params* p) {
   if (n <= 0 || !p) return 0;
   for (int i = 0; i < n; ++i) {
     if (ddflb_workspace_bytes(&p[i]) == 0) return 0;
+    if (p[i].fx != 0.0 || p[i].fy != 0.0 || p[i].force_omega != 0.0) {
+      set_error("the batched step runs unforced instances only (fx = fy = force_omega = 0)");
+      return 0;
+    }
     if (p[i].storage != p[0].storage || p[i].check_every != p[0].check_every) {
       set_error("all instances of a batch share storage and check_every");
       return 0;
@@ -610,6 +614,7 @@ ddflb_status ddflb_batch_init(ddflb_batch* b, int32_t i, const float* rho, const
   L.P = b->lp[i];
   L.P_bc = p.bc;
   L.storage = p.storage;
+  L.force = false;
   L.block = dim3(128, 1, 1);
   L.stream = b->stream;
   InitPtrs in{rho, ux, uy, phi, grads};
@@ -660,6 +665,7 @@ ddflb_status ddflb_batch_fields(ddflb_batch* b, int32_t i, float* rho, float* ux
   L.P = b->lp[i];
   L.P_bc = b->p[i].bc;
   L.storage = b->p[i].storage;
+  L.force = false;
   L.block = dim3(128, 1, 1);
   L.stream = b->stream;
   const char* f = b->ws + ((t & 1) ? b->lay.off_buf1[i] : b->lay.off_buf0[i]);

@@ -2,7 +2,8 @@
 //
 // Method: Hajabdollahi & Premnath, arXiv 1908.06742.
 //   Sec. 2  flow MRT collision in the non-orthogonal basis (Eqs. basisvectors,
-//           MRT-LBEfluidmotion_transformed, eqmrawmoment), F = 0
+//           MRT-LBEfluidmotion_transformed, eqmrawmoment), with the body-force
+//           source moments when a force acts
 //   Sec. 3  scalar MRT collision with anisotropic third-order equilibria
 //           (Eqs. MRT-LBECDE, eqmrawmoment_CDE)
 //   Sec. 4  local strain rate and vorticity from non-equilibrium moments
@@ -44,6 +45,9 @@ struct LbParams {
   float lid[9];           // moving-wall momentum term 2 w_a rho0 e_ax u_lid / c_s^2 (deviation form)
   float abb_lid[9];       // anti-bounce-back source 2 w^phi_a (phi_lid - phi0)
   float abb_wall[9];      // anti-bounce-back source 2 w^phi_a (phi_wall - phi0)
+  // body force (Sec. 2): F = (fx + field_x, fy + field_y) * fmod at every node
+  float fx, fy, fmod;
+  const float* ffield;    // optional [2][ny][nx] (row stride nx), or null
 };
 
 // Device status block (one per lattice pair), written by the reductions.
@@ -216,7 +220,8 @@ __device__ __forceinline__ void populations(float k0, float kx, float ky, float 
   d[8] = 0.25f * (r - s);
 }
 
-// Macroscopic state of a node (Eq. hydrodynamic_fields with F = 0; phi = sum g).
+// Macroscopic state of a node (Eq. hydrodynamic_fields; phi = sum g).  Without
+// a force u = j / rho; macro_force below adds the half-force shift first.
 struct Macro {
   float rho, irho, ux, uy, phi;
 };
@@ -276,7 +281,7 @@ __device__ __forceinline__ Neq neq_scalar(const LbParams& P, const Mom& g, const
 }
 
 // Collision in increment form: f*_a = f_a - [T^-1 Lambda (m - m^eq)]_a
-// (Eqs. MRT-LBEfluidmotion_transformed with F = 0, MRT-LBECDE), so that only
+// (Eqs. MRT-LBEfluidmotion_transformed without force, MRT-LBECDE), so that only
 // the small increment is built from moments and the stored value is rounded
 // once.  w[] holds the relaxation rates of the lattice (w[0] = 0).
 __device__ __forceinline__ void relax(const float w[9], const Neq& n, float d[9]) {
@@ -293,6 +298,125 @@ __device__ __forceinline__ void relax(const float w[9], const Neq& n, float d[9]
   d[6] -= 0.25f * (r + s);
   d[7] -= 0.25f * (p - q);
   d[8] -= 0.25f * (r - s);
+}
+
+// ------------------------------------------------------------ body force
+// Sec. 2: the stored flow populations are f-bar = f - S/2, which makes the
+// trapezoidal source explicit (Eq. MRT-LBEfluidmotion_transformed):
+//   u = (sum f-bar e + F/2) / rho                      (Eq. hydrodynamic_fields)
+//   m-bar* = m-bar - Lambda (m-bar - m^eq) + (I - Lambda/2) S
+// with the source moments S of the force (the sigma' list after Eq. eqmrawmoment).
+struct Force {
+  float x, y;
+};
+
+__device__ __forceinline__ Force node_force(const LbParams& P, int x, int y) {
+  float fx = P.fx, fy = P.fy;
+  if (P.ffield != nullptr) {
+    const int64_t c = (int64_t)y * P.nx + x, n = (int64_t)P.nx * P.ny;
+    fx += P.ffield[c];
+    fy += P.ffield[n + c];
+  }
+  return Force{fx * P.fmod, fy * P.fmod};
+}
+
+// Macroscopic state with the half-force velocity shift; the returned Mom has
+// kx, ky replaced by rho u (what the equilibria and non-equilibria need).
+__device__ __forceinline__ Macro macro_force(const LbParams& P, Mom& mf, const Mom& mg,
+                                             const Force& F) {
+  mf.kx += 0.5f * F.x;
+  mf.ky += 0.5f * F.y;
+  return macro(P, mf, mg);
+}
+
+struct Src {
+  float s1, s2, s3, s4, s5, s6, s7, s8;
+};
+
+__device__ __forceinline__ Src source(const Force& F, const Macro& q) {
+  Src s;
+  const float sxx = 2.0f * F.x * q.ux, syy = 2.0f * F.y * q.uy;
+  s.s1 = F.x;
+  s.s2 = F.y;
+  s.s3 = sxx + syy;
+  s.s4 = sxx - syy;
+  s.s5 = F.x * q.uy + F.y * q.ux;
+  s.s6 = F.y * q.ux * q.ux + 2.0f * F.x * q.ux * q.uy;
+  s.s7 = F.x * q.uy * q.uy + 2.0f * F.y * q.uy * q.ux;
+  s.s8 = 2.0f * (F.x * q.ux * q.uy * q.uy + F.y * q.uy * q.ux * q.ux);
+  return s;
+}
+
+// Forced collision increment: f-bar* = f-bar - T^-1 [Lambda n - (I - Lambda/2) S].
+// With w1 = w2 = 0 the momentum gains exactly F (through d1, d2 = -F).
+__device__ __forceinline__ void relax_source(const float w[9], const Neq& n, const Src& s,
+                                             float d[9]) {
+  const float d1 = w[1] * n.n1 - (1.0f - 0.5f * w[1]) * s.s1;
+  const float d2 = w[2] * n.n2 - (1.0f - 0.5f * w[2]) * s.s2;
+  const float d3 = w[3] * n.n3 - (1.0f - 0.5f * w[3]) * s.s3;
+  const float d4 = w[4] * n.n4 - (1.0f - 0.5f * w[4]) * s.s4;
+  const float d5 = w[5] * n.n5 - (1.0f - 0.5f * w[5]) * s.s5;
+  const float d6 = w[6] * n.n6 - (1.0f - 0.5f * w[6]) * s.s6;
+  const float d7 = w[7] * n.n7 - (1.0f - 0.5f * w[7]) * s.s7;
+  const float d8 = w[8] * n.n8 - (1.0f - 0.5f * w[8]) * s.s8;
+  const float dxx = 0.5f * (d3 + d4), dyy = 0.5f * (d3 - d4);
+  d[0] -= d8 - d3;
+  d[1] -= 0.5f * (d1 + dxx - d7 - d8);
+  d[2] -= 0.5f * (d2 + dyy - d6 - d8);
+  d[3] -= 0.5f * (-d1 + dxx + d7 - d8);
+  d[4] -= 0.5f * (-d2 + dyy + d6 - d8);
+  const float p = d5 + d8, q = d6 + d7, r = d8 - d5, s2 = d6 - d7;
+  d[5] -= 0.25f * (p + q);
+  d[6] -= 0.25f * (r + s2);
+  d[7] -= 0.25f * (p - q);
+  d[8] -= 0.25f * (r - s2);
+}
+
+// Moments, macroscopic state and both collisions of one node, in place on the
+// pulled deviations df, dg.  FORCE = false is the unforced step.
+template <bool FORCE>
+__device__ __forceinline__ void collide(const LbParams& P, int x, int y, float df[9],
+                                        float dg[9]) {
+  Mom mf = moments_flow(df);
+  const Mom mg = moments_scalar(dg);
+  if (FORCE) {
+    const Force F = node_force(P, x, y);
+    const Macro q = macro_force(P, mf, mg, F);
+    relax_source(P.wf, neq_flow(mf, q), source(F, q), df);
+    relax(P.wg, neq_scalar(P, mg, mf, q), dg);
+  } else {
+    const Macro q = macro(P, mf, mg);
+    relax(P.wf, neq_flow(mf, q), df);
+    relax(P.wg, neq_scalar(P, mg, mf, q), dg);
+  }
+}
+
+// Macroscopic state and the non-equilibrium moments the kinematics use.  With
+// a force the flow moments are those of f = f-bar + S/2 (the distribution whose
+// non-equilibrium part Sec. 4 relates to the velocity gradients).
+template <bool FORCE>
+__device__ __forceinline__ Macro state(const LbParams& P, int x, int y, const float df[9],
+                                       const float dg[9], Neq& nf, Neq& ng) {
+  Mom mf = moments_flow(df);
+  const Mom mg = moments_scalar(dg);
+  Macro q;
+  if (FORCE) {
+    const Force F = node_force(P, x, y);
+    q = macro_force(P, mf, mg, F);
+    nf = neq_flow(mf, q);
+    const Src s = source(F, q);
+    nf.n3 += 0.5f * s.s3;
+    nf.n4 += 0.5f * s.s4;
+    nf.n5 += 0.5f * s.s5;
+    nf.n6 += 0.5f * s.s6;
+    nf.n7 += 0.5f * s.s7;
+    nf.n8 += 0.5f * s.s8;
+  } else {
+    q = macro(P, mf, mg);
+    nf = neq_flow(mf, q);
+  }
+  ng = neq_scalar(P, mg, mf, q);
+  return q;
 }
 
 // ------------------------------------------------------------ local kinematics

@@ -24,6 +24,7 @@ struct Launch {
   LbParams P;
   int P_bc;
   int storage;  // 0 fp32, 1 fp16, 2 bf16
+  bool force;   // a body force acts (the FORCE kernel variants)
   dim3 block;
   cudaStream_t stream;
 };

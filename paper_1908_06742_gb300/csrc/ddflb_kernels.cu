@@ -20,7 +20,7 @@
 namespace ddflb {
 
 // ------------------------------------------------------------------ step
-template <typename S, int BC>
+template <typename S, int BC, bool FORCE>
 __global__ void __launch_bounds__(256) k_step(LbParams P, const S* __restrict__ fin,
                                               const S* __restrict__ gin, S* __restrict__ fout,
                                               S* __restrict__ gout,
@@ -31,10 +31,7 @@ __global__ void __launch_bounds__(256) k_step(LbParams P, const S* __restrict__ 
   if (status != nullptr && status->diverged) return;
   float df[9], dg[9];
   pull<S, BC>(P, fin, gin, x, y, df, dg);
-  const Mom mf = moments_flow(df), mg = moments_scalar(dg);
-  const Macro q = macro(P, mf, mg);
-  relax(P.wf, neq_flow(mf, q), df);
-  relax(P.wg, neq_scalar(P, mg, mf, q), dg);
+  collide<FORCE>(P, x, y, df, dg);
   const int64_t o = (int64_t)y * P.pitch + x;
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
@@ -44,7 +41,7 @@ __global__ void __launch_bounds__(256) k_step(LbParams P, const S* __restrict__ 
 }
 
 // ------------------------------------------------------------------ fields
-template <typename S, int BC>
+template <typename S, int BC, bool FORCE>
 __global__ void __launch_bounds__(256) k_fields(LbParams P, const S* __restrict__ fin,
                                                 const S* __restrict__ gin, FieldPtrs out) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -52,9 +49,9 @@ __global__ void __launch_bounds__(256) k_fields(LbParams P, const S* __restrict_
   if (x >= P.nx || y >= P.ny) return;
   float df[9], dg[9];
   pull<S, BC>(P, fin, gin, x, y, df, dg);
-  const Mom mf = moments_flow(df), mg = moments_scalar(dg);
-  const Macro q = macro(P, mf, mg);
-  const Kin k = kinematics(P, neq_flow(mf, q), neq_scalar(P, mg, mf, q), q);
+  Neq nf, ng;
+  const Macro q = state<FORCE>(P, x, y, df, dg, nf, ng);
+  const Kin k = kinematics(P, nf, ng, q);
   const int64_t o = (int64_t)y * P.nx + x;
   if (out.p[0]) out.p[0][o] = q.rho;
   if (out.p[1]) out.p[1][o] = q.ux;
@@ -89,7 +86,7 @@ __global__ void __launch_bounds__(256) k_pops(LbParams P, const S* __restrict__ 
 // the first pull will read: direction a goes to the upstream node x - e_a if
 // that node exists (periodic wrap included), otherwise (a wall link) into the
 // node's own slot of the opposite direction, with the wall rule undone.
-template <typename S, int BC>
+template <typename S, int BC, bool FORCE>
 __global__ void __launch_bounds__(256) k_init(LbParams P, InitPtrs in, S* __restrict__ fout,
                                               S* __restrict__ gout) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -117,9 +114,23 @@ __global__ void __launch_bounds__(256) k_init(LbParams P, InitPtrs in, S* __rest
     e2 += -c / P.wg[2] * dyph;
     e5 += -c / P.wg[5] * (phi * (P.b1 * dxuy + P.b2 * dyux) + P.b1 * uy * dxph + P.b2 * ux * dyph);
   }
+  float m1 = jx, m2 = jy, m6 = jy * (c + uxx), m7 = jx * (c + uyy);
+  float m8 = c * c * k0 + rho * (c * usq + uxx * uyy);
+  if (FORCE) {
+    // the flow populations held are f-bar = f - S/2, S at the force of t = 0
+    const Macro v{rho, 0.0f, ux, uy, phi};
+    const Src s = source(node_force(P, x, y), v);
+    m1 -= 0.5f * s.s1;
+    m2 -= 0.5f * s.s2;
+    m3 -= 0.5f * s.s3;
+    m4 -= 0.5f * s.s4;
+    m5 -= 0.5f * s.s5;
+    m6 -= 0.5f * s.s6;
+    m7 -= 0.5f * s.s7;
+    m8 -= 0.5f * s.s8;
+  }
   float df[9], dg[9];
-  populations(k0, jx, jy, m3, m4, m5, jy * (c + uxx), jx * (c + uyy),
-              c * c * k0 + rho * (c * usq + uxx * uyy), df);
+  populations(k0, m1, m2, m3, m4, m5, m6, m7, m8, df);
   populations(n0, e1, e2, e3, e4, e5, py * (P.b1 * c + uxx), px * (P.b2 * c + uyy),
               c * c * n0 + phi * (c * usq + uxx * uyy), dg);
   constexpr int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
@@ -160,7 +171,7 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-template <typename S, int BC>
+template <typename S, int BC, bool FORCE>
 __global__ void __launch_bounds__(kReduceThreads) k_reduce(LbParams P, const S* __restrict__ fin,
                                                            const S* __restrict__ gin,
                                                            float* __restrict__ uprev, int mode,
@@ -172,8 +183,9 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(LbParams P, const S* 
     const int y = (int)(c / P.nx), x = (int)(c - (int64_t)y * P.nx);
     float df[9], dg[9];
     pull<S, BC>(P, fin, gin, x, y, df, dg);
-    const Mom mf = moments_flow(df), mg = moments_scalar(dg);
-    const Macro q = macro(P, mf, mg);
+    Mom mf = moments_flow(df);
+    const Mom mg = moments_scalar(dg);
+    const Macro q = FORCE ? macro_force(P, mf, mg, node_force(P, x, y)) : macro(P, mf, mg);
     s[0] += (double)mf.k0;
     s[1] += (double)mg.k0;
     s[2] += (double)q.ux * q.ux + (double)q.uy * q.uy;
@@ -236,79 +248,69 @@ dim3 grid2d(const LbParams& P, dim3 b) {
   return dim3((P.nx + b.x - 1) / b.x, (P.ny + b.y - 1) / b.y);
 }
 
-template <typename S>
-cudaError_t step_bc(const Launch& L, const void* fin, const void* gin, void* fout, void* gout,
-                    const DevStatus* st) {
-  const dim3 b = L.block, g = grid2d(L.P, b);
-  switch (L.P_bc) {
-    case BC_PERIODIC:
-      k_step<S, BC_PERIODIC><<<g, b, 0, L.stream>>>(L.P, (const S*)fin, (const S*)gin, (S*)fout,
-                                                    (S*)gout, st);
-      break;
-    case BC_CAVITY:
-      k_step<S, BC_CAVITY><<<g, b, 0, L.stream>>>(L.P, (const S*)fin, (const S*)gin, (S*)fout,
-                                                  (S*)gout, st);
-      break;
-    default:
-      k_step<S, BC_CHANNEL><<<g, b, 0, L.stream>>>(L.P, (const S*)fin, (const S*)gin, (S*)fout,
-                                                   (S*)gout, st);
-  }
-  return cudaGetLastError();
-}
-
-template <typename S, int BC>
-cudaError_t other_bc(const Launch& L, int what, const void* fin, const void* gin, void* a,
-                     void* b, const FieldPtrs* fp, const InitPtrs* ip, int mode, double* partials,
-                     int nparts) {
+template <typename S, int BC, bool FORCE>
+cudaError_t run(const Launch& L, int what, const void* fin, const void* gin, void* a, void* b,
+                const FieldPtrs* fp, const InitPtrs* ip, int mode, double* partials, int nparts,
+                const DevStatus* st) {
   const dim3 blk = L.block, g = grid2d(L.P, blk);
   switch (what) {
     case 0:
-      k_fields<S, BC><<<g, blk, 0, L.stream>>>(L.P, (const S*)fin, (const S*)gin, *fp);
+      k_fields<S, BC, FORCE><<<g, blk, 0, L.stream>>>(L.P, (const S*)fin, (const S*)gin, *fp);
       break;
     case 1:
       k_pops<S, BC><<<g, blk, 0, L.stream>>>(L.P, (const S*)fin, (const S*)gin, (float*)a,
                                              (float*)b);
       break;
     case 2:
-      k_init<S, BC><<<g, blk, 0, L.stream>>>(L.P, *ip, (S*)a, (S*)b);
+      k_init<S, BC, FORCE><<<g, blk, 0, L.stream>>>(L.P, *ip, (S*)a, (S*)b);
+      break;
+    case 3:
+      k_reduce<S, BC, FORCE><<<nparts, kReduceThreads, 0, L.stream>>>(
+          L.P, (const S*)fin, (const S*)gin, (float*)a, mode, partials);
       break;
     default:
-      k_reduce<S, BC><<<nparts, kReduceThreads, 0, L.stream>>>(L.P, (const S*)fin, (const S*)gin,
-                                                               (float*)a, mode, partials);
+      k_step<S, BC, FORCE><<<g, blk, 0, L.stream>>>(L.P, (const S*)fin, (const S*)gin, (S*)a,
+                                                    (S*)b, st);
   }
   return cudaGetLastError();
 }
 
+template <typename S, int BC>
+cudaError_t run_f(const Launch& L, int what, const void* fin, const void* gin, void* a, void* b,
+                  const FieldPtrs* fp, const InitPtrs* ip, int mode, double* partials, int np,
+                  const DevStatus* st) {
+  if (L.force) return run<S, BC, true>(L, what, fin, gin, a, b, fp, ip, mode, partials, np, st);
+  return run<S, BC, false>(L, what, fin, gin, a, b, fp, ip, mode, partials, np, st);
+}
+
 template <typename S>
-cudaError_t other(const Launch& L, int what, const void* fin, const void* gin, void* a, void* b,
-                  const FieldPtrs* fp, const InitPtrs* ip, int mode, double* partials, int np) {
+cudaError_t run_bc(const Launch& L, int what, const void* fin, const void* gin, void* a, void* b,
+                   const FieldPtrs* fp, const InitPtrs* ip, int mode, double* partials, int np,
+                   const DevStatus* st) {
   switch (L.P_bc) {
     case BC_PERIODIC:
-      return other_bc<S, BC_PERIODIC>(L, what, fin, gin, a, b, fp, ip, mode, partials, np);
+      return run_f<S, BC_PERIODIC>(L, what, fin, gin, a, b, fp, ip, mode, partials, np, st);
     case BC_CAVITY:
-      return other_bc<S, BC_CAVITY>(L, what, fin, gin, a, b, fp, ip, mode, partials, np);
+      return run_f<S, BC_CAVITY>(L, what, fin, gin, a, b, fp, ip, mode, partials, np, st);
     default:
-      return other_bc<S, BC_CHANNEL>(L, what, fin, gin, a, b, fp, ip, mode, partials, np);
+      return run_f<S, BC_CHANNEL>(L, what, fin, gin, a, b, fp, ip, mode, partials, np, st);
   }
 }
 
 cudaError_t dispatch(const Launch& L, int what, const void* fin, const void* gin, void* a, void* b,
-                     const FieldPtrs* fp, const InitPtrs* ip, int mode, double* partials, int np) {
+                     const FieldPtrs* fp, const InitPtrs* ip, int mode, double* partials, int np,
+                     const DevStatus* st = nullptr) {
   switch (L.storage) {
-    case 0: return other<float>(L, what, fin, gin, a, b, fp, ip, mode, partials, np);
-    case 1: return other<__half>(L, what, fin, gin, a, b, fp, ip, mode, partials, np);
-    default: return other<__nv_bfloat16>(L, what, fin, gin, a, b, fp, ip, mode, partials, np);
+    case 0: return run_bc<float>(L, what, fin, gin, a, b, fp, ip, mode, partials, np, st);
+    case 1: return run_bc<__half>(L, what, fin, gin, a, b, fp, ip, mode, partials, np, st);
+    default: return run_bc<__nv_bfloat16>(L, what, fin, gin, a, b, fp, ip, mode, partials, np, st);
   }
 }
 }  // namespace
 
 cudaError_t launch_step(const Launch& L, const void* fin, const void* gin, void* fout, void* gout,
                         const DevStatus* st) {
-  switch (L.storage) {
-    case 0: return step_bc<float>(L, fin, gin, fout, gout, st);
-    case 1: return step_bc<__half>(L, fin, gin, fout, gout, st);
-    default: return step_bc<__nv_bfloat16>(L, fin, gin, fout, gout, st);
-  }
+  return dispatch(L, 4, fin, gin, fout, gout, nullptr, nullptr, 0, nullptr, 0, st);
 }
 
 cudaError_t launch_fields(const Launch& L, const void* fin, const void* gin, const FieldPtrs& out) {

@@ -44,6 +44,7 @@ class Params(ctypes.Structure):
         ("phi_min", ctypes.c_double),
         ("scale_f", ctypes.c_double), ("scale_g", ctypes.c_double),
         ("check_every", ctypes.c_int32), ("flags", ctypes.c_int32),
+        ("fx", ctypes.c_double), ("fy", ctypes.c_double), ("force_omega", ctypes.c_double),
     ]
 
 
@@ -90,6 +91,7 @@ SIGNATURES = {
     "ddflb_autotune": (ctypes.c_int, [_VP, ctypes.c_int32] + [ctypes.POINTER(ctypes.c_int32)] * 3 +
                        [ctypes.POINTER(ctypes.c_double)]),
     "ddflb_set_block": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32]),
+    "ddflb_set_force_field": (ctypes.c_int, [_VP, _FP]),
     # warm-start surrogate network kernels
     "ddflb_nn_gemm": (ctypes.c_int, [_FP, _FP] + [ctypes.c_int32] * 5 +
                       [_FP, ctypes.c_int32, _FP, ctypes.c_int32, _FP] + [ctypes.c_int32] * 3 +
@@ -175,6 +177,9 @@ class Config:
     host_io: bool = False
     omega_f: Optional[tuple] = None   # explicit 9-entry diagonals override the above
     omega_g: Optional[tuple] = None
+    fx: float = 0.0             # body force (Sec. 2), times cos(force_omega t)
+    fy: float = 0.0
+    force_omega: float = 0.0
 
     def rates(self):
         wf = self.omega_f or (0.0, 0.0, 0.0, self.omega_bulk, relaxation_rate(self.nu, self.cs2),
@@ -201,6 +206,7 @@ class Config:
         p.scale_f, p.scale_g = self.scale_f, self.scale_g
         p.check_every = self.check_every
         p.flags = FLAG_HOST_IO if self.host_io else 0
+        p.fx, p.fy, p.force_omega = self.fx, self.fy, self.force_omega
         return p
 
 
@@ -322,6 +328,13 @@ class Lattice:
         if cache:
             tuning.store(key, rec)
         return rec
+
+    def set_force_field(self, field):
+        """Spatially varying body force [2, ny, nx] (F_x, F_y) added to (fx, fy);
+        kept alive by this object.  None removes it."""
+        self._force = None if field is None else self._dev(field).reshape(2, *self.shape).contiguous()
+        _check(self.lib.ddflb_set_force_field(self._h, _dptr(self._force)))
+        return self
 
     def set_path(self, path: int):
         """Step kernel variant: 0 automatic, 1 one node per thread, 2 paired nodes."""

@@ -96,3 +96,39 @@ def test_binding_fails_loudly_without_library(tmp_path):
             D.load(str(tmp_path / "missing.so"))
     finally:
         D._lib = old
+
+
+def test_params_struct_layout_matches_header(tmp_path):
+    """The ctypes mirror has the size and field offsets the C compiler gives
+    ddflb_params (compiled here with gcc against include/ddflb.h)."""
+    fields = [f[0] for f in D.Params._fields_]
+    src = ['#include <stddef.h>', '#include <stdio.h>', '#include "ddflb.h"', "int main(void) {",
+           'printf("%zu\\n", sizeof(ddflb_params));']
+    src += [f'printf("%zu\\n", offsetof(ddflb_params, {f}));' for f in fields]
+    src += ["return 0;", "}"]
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(src))
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)], check=True)
+    out = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
+                                          text=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(D.Params)
+    assert out[1:] == [getattr(D.Params, f).offset for f in fields]
+
+
+def test_force_parameters_validated(lib):
+    p = good().to_c()
+    p.fx = float("nan")
+    assert lib.ddflb_workspace_bytes(ctypes.byref(p)) == 0
+    assert "body force" in lib.ddflb_last_error().decode()
+
+
+def test_batch_and_noalloc_reject_forcing(lib):
+    c = good(); c.fx = 1e-6
+    arr = (D.Params * 2)(good().to_c(), c.to_c())
+    assert lib.ddflb_batch_workspace_bytes(2, arr) == 0
+    assert "unforced" in lib.ddflb_last_error().decode()
+    p = c.to_c()
+    out = lib.ddflb_reduce_noalloc(ctypes.byref(p), 4096, 1 << 30, 0, 4096, None)
+    assert out == D.EINVAL and "unforced" in lib.ddflb_last_error().decode()
