@@ -152,6 +152,24 @@ ddflb_status ddflb_step(ddflb_ctx* c, int64_t n);
 ddflb_status ddflb_fields(ddflb_ctx* c, float* rho, float* ux, float* uy, float* phi,
                           float* sxx, float* sxy, float* syy, float* omega);
 
+/* Further local fields of the current state in one pass, each into a [ny][nx]
+ * device float buffer (any pointer may be NULL):
+ *  - the full velocity gradient d_x u_x, d_y u_x, d_x u_y, d_y u_y: diagonal
+ *    parts from Eqs. (diagvelderivativeresult1), (diagvelderivativeresult2),
+ *    the cross derivatives from Eqs. (offdiagvelderivativeresult1),
+ *    (offdiagvelderivativeresult2);
+ *  - the scalar gradient d_x phi, d_y phi from the first-order scalar
+ *    non-equilibrium moments (Eqs. 1stnoneqmmomentx_CDE, 1stnoneqmmomenty_CDE);
+ *  - the velocity-gradient invariants and the Lamb vector named in Sec. 1,
+ *    Q = -S_ij S_ij / 2 + omega_k omega_k / 4,
+ *    R = (S_ij S_jk S_ki + 3/4 omega_i omega_j S_ij) / 3 and L = omega x u,
+ *    for the planar flow (omega along z, so R = S_ij S_jk S_ki / 3 and
+ *    L = (-omega u_y, omega u_x)).
+ * Quantities that need omega are NaN where |phi| < phi_min. */
+ddflb_status ddflb_derived(ddflb_ctx* c, float* dxux, float* dyux, float* dxuy, float* dyuy,
+                           float* dxphi, float* dyphi, float* q, float* r, float* lamb_x,
+                           float* lamb_y);
+
 /* ddflb_fields into HOST buffers (staged; requires DDFLB_FLAG_HOST_IO).  The
  * copies are queued on the context stream; the call synchronises it before
  * returning so the host buffers hold the result. */

@@ -191,6 +191,38 @@ FIELD_NAMES = ("rho", "ux", "uy", "phi", "sxx", "sxy", "syy", "omega")
 EXTRA_NAMES = ("dxux", "dyux", "dxuy", "dyuy", "nxy", "nxy_phi", "dxphi", "dyphi")
 
 
+def derived(fields: dict) -> dict:
+    """Velocity-gradient invariants and the Lamb vector named in Sec. 1, from
+    the oracle's ``fields(extra=True)``: the gradient tensor A_ij = d_j u_i is
+    embedded in 3-D (no z dependence, u_z = 0) and the definitions are
+    evaluated as written with the Levi-Civita tensor:
+      S = (A + A^T)/2,  omega_i = eps_ijk d_j u_k,
+      Q = -S_ij S_ij / 2 + omega_k omega_k / 4,
+      R = (S_ij S_jk S_ki + 3/4 omega_i omega_j S_ij) / 3,
+      L_i = eps_ijk omega_j u_k.
+    Also returns the gradients (dxux, dyux, dxuy, dyuy, dxphi, dyphi)."""
+    ny, nx = fields["ux"].shape
+    G = np.zeros((ny, nx, 3, 3))     # G[..., j, k] = d_j u_k
+    G[..., 0, 0] = fields["dxux"]; G[..., 1, 0] = fields["dyux"]
+    G[..., 0, 1] = fields["dxuy"]; G[..., 1, 1] = fields["dyuy"]
+    A = np.swapaxes(G, -1, -2)       # A[..., i, j] = d_j u_i
+    S = 0.5 * (A + np.swapaxes(A, -1, -2))
+    eps = np.zeros((3, 3, 3))
+    for i, j, k in ((0, 1, 2), (1, 2, 0), (2, 0, 1)):
+        eps[i, j, k] = 1.0
+        eps[i, k, j] = -1.0
+    om = np.einsum("ijk,...jk->...i", eps, G)
+    u = np.stack([fields["ux"], fields["uy"], np.zeros_like(fields["ux"])], axis=-1)
+    Q = -0.5 * np.einsum("...ij,...ij->...", S, S) + 0.25 * np.einsum("...k,...k->...", om, om)
+    R = (np.einsum("...ij,...jk,...ki->...", S, S, S) +
+         0.75 * np.einsum("...i,...j,...ij->...", om, om, S)) / 3.0
+    Lv = np.einsum("ijk,...j,...k->...i", eps, om, u)
+    return {"dxux": fields["dxux"], "dyux": fields["dyux"], "dxuy": fields["dxuy"],
+            "dyuy": fields["dyuy"], "dxphi": fields["dxphi"], "dyphi": fields["dyphi"],
+            "q": Q, "r": R, "lamb_x": Lv[..., 0], "lamb_y": Lv[..., 1], "omega_z": om[..., 2],
+            "lamb_z": Lv[..., 2]}
+
+
 class OracleLattice:
     """Two D2Q9 lattices (flow f, scalar g) advanced in FP64 on the CPU."""
 

@@ -361,6 +361,18 @@ ddflb_status ddflb_fields(ddflb_ctx* c, float* rho, float* ux, float* uy, float*
   return check_launch(launch_fields(c->L, fptr(c, c->cur), gptr(c, c->cur), fp), "fields");
 }
 
+ddflb_status ddflb_derived(ddflb_ctx* c, float* dxux, float* dyux, float* dxuy, float* dyuy,
+                           float* dxphi, float* dyphi, float* q, float* r, float* lamb_x,
+                           float* lamb_y) {
+  if (!c) return fail(DDFLB_EINVAL, "NULL handle");
+  FieldPtrs fp{};
+  float* d[10] = {dxux, dyux, dxuy, dyuy, dxphi, dyphi, q, r, lamb_x, lamb_y};
+  for (int k = 0; k < 10; ++k) fp.p[8 + k] = d[k];
+  fp.derived = 1;
+  at_time(c, c->step);
+  return check_launch(launch_fields(c->L, fptr(c, c->cur), gptr(c, c->cur), fp), "derived");
+}
+
 ddflb_status ddflb_fields_host(ddflb_ctx* c, float* rho, float* ux, float* uy, float* phi,
                                float* sxx, float* sxy, float* syy, float* omega) {
   if (!c) return fail(DDFLB_EINVAL, "NULL handle");

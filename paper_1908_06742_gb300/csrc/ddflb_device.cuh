@@ -427,6 +427,9 @@ __device__ __forceinline__ Macro state(const LbParams& P, int x, int y, const fl
 //   omega_z = (2 N^phi - (b1 + b2) N) / (b1 - b2);  S_xy = N / 2.
 struct Kin {
   float sxx, sxy, syy, omega;
+  float div;           // d_x u_x + d_y u_y = -w3 nf_3 / (2 c rho), formed without cancellation
+  float dyux, dxuy;    // Eqs. (offdiagvelderivativeresult1), (offdiagvelderivativeresult2)
+  float dxphi, dyphi;  // scalar gradient from the first-order non-equilibrium moments
 };
 
 __device__ __forceinline__ Kin kinematics(const LbParams& P, const Neq& nf, const Neq& ng,
@@ -440,14 +443,45 @@ __device__ __forceinline__ Kin kinematics(const LbParams& P, const Neq& nf, cons
   k.sxx = diag * (P.wf[3] * nf.n3 + P.wf[4] * nf.n4);
   k.syy = diag * (P.wf[3] * nf.n3 - P.wf[4] * nf.n4);
   k.sxy = 0.5f * N;
+  k.div = 2.0f * diag * P.wf[3] * nf.n3;
+  k.dxphi = dxphi;
+  k.dyphi = dyphi;
   if (fabsf(q.phi) >= P.phimin) {
     const float iphi = __frcp_rn(q.phi);
     const float Nphi = (-P.wg[5] * ng.n5 * inv_c - (P.b1 * q.uy * dxphi + P.b2 * q.ux * dyphi)) * iphi;
     k.omega = (2.0f * Nphi - (P.b1 + P.b2) * N) * P.inv_db;
+    k.dxuy = (Nphi - P.b2 * N) * P.inv_db;
+    k.dyux = (P.b1 * N - Nphi) * P.inv_db;
   } else {
     k.omega = __int_as_float(0x7fc00000);  // NaN: the relations need phi != 0
+    k.dxuy = k.omega;
+    k.dyux = k.omega;
   }
   return k;
+}
+
+// Invariants built from the local velocity gradient (the vortex-identification
+// quantities named in Sec. 1), for a planar flow (omega along z, S in the
+// x-y plane, so the omega_i omega_j S_ij term of R vanishes):
+//   Q = -S_ij S_ij / 2 + omega^2 / 4,  R = S_ij S_jk S_ki / 3,
+//   Lamb vector L = omega x u = (-omega u_y, omega u_x).
+// For the 2x2 strain, S_ij S_jk S_ki = tr S (sxx^2 - sxx syy + syy^2 + 3 sxy^2):
+// R is proportional to the divergence, which is small in a nearly incompressible
+// flow, so it is formed from tr S directly (one moment, n_3) rather than as the
+// difference sxx^3 + syy^3 of two nearly opposite cubes.
+struct Inv {
+  float q, r, lx, ly;
+};
+
+__device__ __forceinline__ Inv invariants(const Kin& k, const Macro& m) {
+  Inv v;
+  const float ss = k.sxx * k.sxx + k.syy * k.syy + 2.0f * k.sxy * k.sxy;
+  v.q = -0.5f * ss + 0.25f * k.omega * k.omega;
+  v.r = k.div * (k.sxx * k.sxx - k.sxx * k.syy + k.syy * k.syy + 3.0f * k.sxy * k.sxy) *
+        (1.0f / 3.0f);
+  v.lx = -k.omega * m.uy;
+  v.ly = k.omega * m.ux;
+  return v;
 }
 
 }  // namespace ddflb

@@ -13,7 +13,10 @@ constexpr int kReduceThreads = 256;
 constexpr int kReduceBlocks = 608;  // 4 per SM on a 152-SM GB300; fixed for deterministic sums
 
 struct FieldPtrs {
-  float* p[8];  // rho, ux, uy, phi, sxx, sxy, syy, omega (any may be null)
+  // 0..7: rho, ux, uy, phi, sxx, sxy, syy, omega; 8..17 (read only if derived):
+  // dxux, dyux, dxuy, dyuy, dxphi, dyphi, Q, R, lamb_x, lamb_y (any may be null)
+  float* p[18];
+  int derived;
 };
 
 struct InitPtrs {

@@ -3,7 +3,8 @@
 //
 //   k_step      one time step: pull both lattices with the wall rules, moments,
 //               MRT collision of both, back-transform, store (Secs. 2, 3, 5)
-//   k_fields    local kinematics of the current state (Sec. 4)
+//   k_fields    local kinematics of the current state (Sec. 4), optionally the
+//               full velocity gradient, scalar gradient, Q, R and Lamb vector
 //   k_pops      current pre-collision populations as full values
 //   k_init      equilibrium + Chapman-Enskog non-equilibrium initial state,
 //               written in the pre-streamed layout the pull step expects
@@ -61,6 +62,13 @@ __global__ void __launch_bounds__(256) k_fields(LbParams P, const S* __restrict_
   if (out.p[5]) out.p[5][o] = k.sxy;
   if (out.p[6]) out.p[6][o] = k.syy;
   if (out.p[7]) out.p[7][o] = k.omega;
+  if (out.derived) {
+    const Inv v = invariants(k, q);
+    const float d[10] = {k.sxx, k.dyux, k.dxuy, k.syy, k.dxphi, k.dyphi, v.q, v.r, v.lx, v.ly};
+#pragma unroll
+    for (int i = 0; i < 10; ++i)
+      if (out.p[8 + i]) out.p[8 + i][o] = d[i];
+  }
 }
 
 // ------------------------------------------------------------------ populations

@@ -23,6 +23,7 @@ BC = {"periodic": 0, "cavity": 1, "channel": 2}
 STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
 FLAG_HOST_IO = 1
 FIELD_NAMES = ("rho", "ux", "uy", "phi", "sxx", "sxy", "syy", "omega")
+DERIVED_NAMES = ("dxux", "dyux", "dxuy", "dyuy", "dxphi", "dyphi", "q", "r", "lamb_x", "lamb_y")
 
 
 class DdflbError(RuntimeError):
@@ -62,6 +63,7 @@ SIGNATURES = {
     "ddflb_step": (ctypes.c_int, [_VP, ctypes.c_int64]),
     "ddflb_fields": (ctypes.c_int, [_VP] + [_FP] * 8),
     "ddflb_fields_host": (ctypes.c_int, [_VP] + [_FP] * 8),
+    "ddflb_derived": (ctypes.c_int, [_VP] + [_FP] * 10),
     "ddflb_populations": (ctypes.c_int, [_VP, _FP, _FP]),
     "ddflb_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double),
@@ -288,6 +290,12 @@ class Lattice:
     def fields(self, names=FIELD_NAMES) -> dict:
         out = {k: (self._empty() if k in names else None) for k in FIELD_NAMES}
         _check(self.lib.ddflb_fields(self._h, *[_dptr(out[k]) for k in FIELD_NAMES]))
+        return {k: v for k, v in out.items() if v is not None}
+
+    def derived(self, names=DERIVED_NAMES) -> dict:
+        """Velocity and scalar gradients, Q, R and the Lamb vector (one pass)."""
+        out = {k: (self._empty() if k in names else None) for k in DERIVED_NAMES}
+        _check(self.lib.ddflb_derived(self._h, *[_dptr(out[k]) for k in DERIVED_NAMES]))
         return {k: v for k, v in out.items() if v is not None}
 
     def fields_host(self, out: dict) -> dict:

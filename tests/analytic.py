@@ -21,7 +21,7 @@ def taylor_green(n, u0, nu, t, ny=None):
     dxuy = u0 * kx * cx * cy * dec
     dyuy = -u0 * ky * sx * sy * dec
     return dict(ux=ux, uy=uy, sxx=dxux, syy=dyuy, sxy=0.5 * (dxuy + dyux),
-                omega=dxuy - dyux)
+                omega=dxuy - dyux, dxux=dxux, dyux=dyux, dxuy=dxuy, dyuy=dyuy)
 
 
 def diffusion_sine(n, amp, D, t):
