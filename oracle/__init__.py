@@ -14,6 +14,8 @@ transport", arXiv 1908.06742.
   * scalar MRT with beta anisotropy ...... Sec. 3, Eqs. (MRT-LBECDE), (eqmrawmoment_CDE)
   * local strain rate and vorticity ...... Sec. 4, Eqs. (crossderivativeRHS1)-(vorticityexpression)
   * walls, lid, fixed scalar, periodic ... Sec. 5
+  * body force (f-bar transformation) ..... Sec. 2, Eq. (MRT-LBEfluidmotion_transformed)
+  * SRT / cascaded / central-moment scalar  Apps. B, C, D
 
 Parity status of each function is recorded in the tests that pin it
 (tests/test_oracle_*.py).  ``fields`` for the lid-driven cavity has no external
@@ -34,6 +36,8 @@ from . import build as _build
 Q = 9
 BC = {"periodic": 0, "cavity": 1, "channel": 2}
 STORAGE = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
+# scalar collision: Sec. 3 MRT, App. B SRT, App. C cascaded, App. D central moments
+SCALAR_MODEL = {"mrt": 0, "srt": 1, "cascaded": 2, "central": 3}
 
 _D = ctypes.POINTER(ctypes.c_double)
 
@@ -50,6 +54,7 @@ class _Params(ctypes.Structure):
         ("phi_min", ctypes.c_double),
         ("scale_f", ctypes.c_double), ("scale_g", ctypes.c_double),
         ("fx", ctypes.c_double), ("fy", ctypes.c_double), ("f_omega", ctypes.c_double),
+        ("scalar_model", ctypes.c_int32), ("pad_", ctypes.c_int32),
     ]
 
 
@@ -117,6 +122,7 @@ class OracleParams:
     fx: float = 0.0                # constant body force (Sec. 2)
     fy: float = 0.0
     f_omega: float = 0.0           # force modulation cos(f_omega t), 0 = steady
+    scalar_model: str = "mrt"      # "mrt" (Sec. 3), "srt" (App. B), "cascaded" (App. C), "central" (App. D)
     lam_override: Optional[tuple] = None      # full 9-entry flow diagonal (tests)
     lam_phi_override: Optional[tuple] = None  # full 9-entry scalar diagonal (tests)
 
@@ -148,6 +154,7 @@ class OracleParams:
         p.phi_min = self.phi_min
         p.scale_f, p.scale_g = self.scale_f, self.scale_g
         p.fx, p.fy, p.f_omega = self.fx, self.fy, self.f_omega
+        p.scalar_model = SCALAR_MODEL[self.scalar_model]
         return p
 
 

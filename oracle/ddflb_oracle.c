@@ -42,6 +42,10 @@ typedef struct {
   double scale_f, scale_g;      /* storage scale for the rounding emulation */
   double fx, fy;                /* constant body force (Sec. 2, F in Eq. momentumeqn) */
   double f_omega;               /* force modulation cos(f_omega t); 0 = steady */
+  int32_t scalar_model;         /* scalar collision: 0 MRT (Sec. 3), 1 SRT (App. B),
+                                   2 cascaded central moments (App. C),
+                                   3 non-cascaded central moments (App. D) */
+  int32_t pad_;
 } orc_params;
 
 /* ---------------------------------------------------------------------------
@@ -198,6 +202,152 @@ static void node_force(const orc_params* p, const double* field, size_t N, size_
   *Fy = (p->fy + (field ? field[N + c] : 0.0)) * mod;
 }
 
+/* ---------------------------------------------------------------------------
+ * Alternative scalar collision models (Apps. B-D).
+ * ------------------------------------------------------------------------- */
+
+/* Bare raw-moment basis P of App. B (Eq. basisvectors1): rows |e_x^m e_y^n> for
+ * (m, n) = (0,0) (1,0) (0,1) (2,0) (0,2) (1,1) (2,1) (1,2) (2,2); the same orders
+ * index the central moments of Eq. (centralmomentdefinitions_CDE). */
+static const int MO[Q] = {0, 1, 0, 2, 0, 1, 2, 1, 2};
+static const int NO[Q] = {0, 0, 1, 0, 2, 1, 1, 2, 2};
+
+static double ipow(double v, int k) {
+  double r = 1.0;
+  for (int i = 0; i < k; ++i) r *= v;
+  return r;
+}
+
+/* Rows of sum_a (.) (e_ax - ux)^m (e_ay - uy)^n: the raw moments for u = 0. */
+static void central_matrix(double ux, double uy, double* C) {
+  for (int j = 0; j < Q; ++j)
+    for (int a = 0; a < Q; ++a) C[j * Q + a] = ipow(EX[a] - ux, MO[j]) * ipow(EY[a] - uy, NO[j]);
+}
+
+/* Raw-moment equilibria of Eq. (eqmrawmoment_CDE) in the bare order of App. B. */
+static void raw_eq_bare(const orc_params* p, double phi, double ux, double uy, double* q) {
+  const double c = p->cs2_phi;
+  q[0] = phi;
+  q[1] = phi * ux;
+  q[2] = phi * uy;
+  q[3] = c * phi + phi * ux * ux;
+  q[4] = c * phi + phi * uy * uy;
+  q[5] = phi * ux * uy;
+  q[6] = p->beta1 * c * phi * uy + phi * ux * ux * uy;
+  q[7] = p->beta2 * c * phi * ux + phi * ux * uy * uy;
+  q[8] = c * c * phi + c * phi * (ux * ux + uy * uy) + phi * ux * ux * uy * uy;
+}
+
+/* Central-moment equilibria, Eq. (eqmcentralmoment_CDE): the local Maxwellian's,
+ * with (beta - 1) anisotropy in the third-order ones. */
+static void central_eq(const orc_params* p, double phi, double ux, double uy, double* e) {
+  const double c = p->cs2_phi;
+  e[0] = phi;
+  e[1] = 0.0;
+  e[2] = 0.0;
+  e[3] = c * phi;
+  e[4] = c * phi;
+  e[5] = 0.0;
+  e[6] = (p->beta1 - 1.0) * c * phi * uy;
+  e[7] = (p->beta2 - 1.0) * c * phi * ux;
+  e[8] = c * c * phi;
+}
+
+/* Solve C g = rhs for g (9 x 9, Gaussian elimination through invert()). */
+static void solve9(const double* C, const double* rhs, double* g) {
+  double Ci[Q * Q];
+  invert(C, Ci, Q);
+  matvec(Ci, rhs, g);
+}
+
+/* App. B: single relaxation time, g~ = g - (g - g^eq)/tau_phi with g^eq = P^-1 q^eq
+ * and 1/tau_phi = lam_phi[1]. */
+static void scalar_srt(const orc_params* p, const double* g, double phi, double ux, double uy,
+                       double* gs) {
+  double P[Q * Q], q[Q], geq[Q];
+  central_matrix(0.0, 0.0, P);
+  raw_eq_bare(p, phi, ux, uy, q);
+  solve9(P, q, geq);
+  const double w = p->lam_phi[1];
+  for (int a = 0; a < Q; ++a) gs[a] = g[a] - w * (g[a] - geq[a]);
+}
+
+/* App. D: every central moment relaxes to its equilibrium at its own rate (the
+ * pair xx, yy through their sum at lam_phi[3] and difference at lam_phi[4]);
+ * the post-collision populations are the ones with those central moments. */
+static void scalar_central(const orc_params* p, const double* g, double phi, double ux,
+                           double uy, double* gs) {
+  double C[Q * Q], k[Q], e[Q], kt[Q];
+  central_matrix(ux, uy, C);
+  matvec(C, g, k);
+  central_eq(p, phi, ux, uy, e);
+  const double* w = p->lam_phi;
+  kt[0] = k[0];
+  kt[1] = k[1] + w[1] * (e[1] - k[1]);
+  kt[2] = k[2] + w[2] * (e[2] - k[2]);
+  const double sum = (k[3] + k[4]) + w[3] * ((e[3] + e[4]) - (k[3] + k[4]));
+  const double dif = (k[3] - k[4]) + w[4] * ((e[3] - e[4]) - (k[3] - k[4]));
+  kt[3] = 0.5 * (sum + dif);
+  kt[4] = 0.5 * (sum - dif);
+  for (int j = 5; j < Q; ++j) kt[j] = k[j] + w[j] * (e[j] - k[j]);
+  solve9(C, kt, gs);
+}
+
+/* App. C: cascaded collision.  The changes h_0..h_8 of the moments are found
+ * order by order so that each central moment relaxes at its rate, then
+ * g~ = g + K h with the orthogonal basis K of Eq. (orthogonalbasisvectors).
+ * Reading: the printed K6 = |e_x^2 e_y>, K7 = |e_x e_y^2> are not orthogonal to
+ * K2, K1 and contradict the printed inner products (<e_x|K h> = 6 h1,
+ * <e_x^2 e_y|K h> = 4 h2 - 4 h6) and the printed expansion of g~; all three are
+ * met by the orthogonal K6 = 2|e_y> - 3|e_x^2 e_y>, K7 = 2|e_x> - 3|e_x e_y^2>. */
+static double kbasis(int j, int ex, int ey) {
+  const double x2 = ex * ex, y2 = ey * ey;
+  switch (j) {
+    case 0: return 1.0;
+    case 1: return ex;
+    case 2: return ey;
+    case 3: return 3.0 * (x2 + y2) - 4.0;
+    case 4: return x2 - y2;
+    case 5: return (double)(ex * ey);
+    case 6: return 2.0 * ey - 3.0 * x2 * ey;
+    case 7: return 2.0 * ex - 3.0 * ex * y2;
+    default: return 9.0 * x2 * y2 - 6.0 * (x2 + y2) + 4.0;
+  }
+}
+
+static void scalar_cascaded(const orc_params* p, const double* g, double phi, double ux,
+                            double uy, double* gs) {
+  double C[Q * Q], k[Q], e[Q], h[Q];
+  central_matrix(ux, uy, C);
+  matvec(C, g, k);            /* pre-collision central moments */
+  central_eq(p, phi, ux, uy, e);
+  const double* w = p->lam_phi;
+  const double ux2 = ux * ux, uy2 = uy * uy;
+  h[0] = 0.0;
+  h[1] = w[1] / 6.0 * (e[1] - k[1]);
+  h[2] = w[2] / 6.0 * (e[2] - k[2]);
+  h[3] = w[3] / 12.0 * ((e[3] + e[4]) - (k[3] + k[4])) + (ux * h[1] + uy * h[2]);
+  h[4] = w[4] / 4.0 * ((e[3] - e[4]) - (k[3] - k[4])) + 3.0 * (ux * h[1] - uy * h[2]);
+  h[5] = w[5] / 4.0 * (e[5] - k[5]) + 1.5 * (ux * h[2] + uy * h[1]);
+  h[6] = -w[6] / 4.0 * (e[6] - k[6]) - 2.0 * ux * h[5] - 0.5 * uy * h[4] - 1.5 * uy * h[3] +
+         (1.0 + 1.5 * ux2) * h[2] + 3.0 * ux * uy * h[1];
+  h[7] = -w[7] / 4.0 * (e[7] - k[7]) - 2.0 * uy * h[5] + 0.5 * ux * h[4] - 1.5 * ux * h[3] +
+         3.0 * ux * uy * h[2] + (1.0 + 1.5 * uy2) * h[1];
+  h[8] = w[8] / 4.0 * (e[8] - k[8]) - 2.0 * ux * h[7] - 2.0 * uy * h[6] - 4.0 * ux * uy * h[5] +
+         0.5 * (ux2 - uy2) * h[4] - (2.0 + 1.5 * (ux2 + uy2)) * h[3] +
+         (2.0 + 3.0 * ux2) * uy * h[2] + (2.0 + 3.0 * uy2) * ux * h[1];
+  for (int a = 0; a < Q; ++a) {
+    double d = 0.0;
+    for (int j = 0; j < Q; ++j) d += kbasis(j, EX[a], EY[a]) * h[j];
+    gs[a] = g[a] + d;
+  }
+}
+
+/* Scalar relaxation rate j as the model uses it (SRT: the single rate lam_phi[1]). */
+static double wphi(const orc_params* p, int j) {
+  return p->scalar_model == 1 ? p->lam_phi[1] : p->lam_phi[j];
+}
+
 /* The populations held are f-bar = f - S/2 (the transformation that makes the
  * trapezoidal source explicit, Sec. 2), so u = (sum f-bar e + F/2) / rho
  * (Eq. hydrodynamic_fields) and the collision of Eq.
@@ -216,7 +366,12 @@ static void collide_node(const orc_params* p, const double* f, const double* g,
     ns[k] = n[k] - p->lam_phi[k] * (n[k] - neq[k]);
   }
   matvec(TI_, ms, fs);
-  matvec(TI_, ns, gs);
+  switch (p->scalar_model) {
+    case 1: scalar_srt(p, g, phi, ux, uy, gs); break;
+    case 2: scalar_cascaded(p, g, phi, ux, uy, gs); break;
+    case 3: scalar_central(p, g, phi, ux, uy, gs); break;
+    default: matvec(TI_, ns, gs);
+  }
 }
 
 static int opposite(int a) {
@@ -334,6 +489,14 @@ void orc_init(const orc_params* p, const double* rho, const double* ux, const do
     source_m(Fx, Fy, vx, vy, S);
     for (int k = 0; k < Q; ++k) m[k] -= 0.5 * S[k];
     eq_scalar(ph, vx, vy, cp2, p->beta1, p->beta2, n);
+    /* central-moment models: the equilibrium is the raw image of the central
+     * equilibria, and the first-order non-equilibrium parts are those of the
+     * central moments (reading: the Chapman-Enskog expansion of a central-moment
+     * collision gives eta_x^(1), eta_y^(1) as for the MRT and
+     * eta_xy^(1) = -(c/w5)[phi N^phi + (b1 - 1) uy dxphi + (b2 - 1) ux dyphi]) */
+    double e[Q];
+    const int central = p->scalar_model >= 2;
+    if (central) central_eq(p, ph, vx, vy, e);
     if (grads) {
       double dxux = grads[0 * N + c], dyux = grads[1 * N + c];
       double dxuy = grads[2 * N + c], dyuy = grads[3 * N + c];
@@ -341,14 +504,26 @@ void orc_init(const orc_params* p, const double* rho, const double* ux, const do
       m[3] += -(2.0 * cs2 * r / p->lam[3]) * (dxux + dyuy);
       m[4] += -(2.0 * cs2 * r / p->lam[4]) * (dxux - dyuy);
       m[5] += -(cs2 * r / p->lam[5]) * (dxuy + dyux);
-      n[1] += -(cp2 / p->lam_phi[1]) * dxph;
-      n[2] += -(cp2 / p->lam_phi[2]) * dyph;
-      n[5] += -(cp2 / p->lam_phi[5]) *
-              (ph * (p->beta1 * dxuy + p->beta2 * dyux) + p->beta1 * vy * dxph +
-               p->beta2 * vx * dyph);
+      const double Nphi = ph * (p->beta1 * dxuy + p->beta2 * dyux);
+      if (central) {
+        e[1] += -(cp2 / wphi(p, 1)) * dxph;
+        e[2] += -(cp2 / wphi(p, 2)) * dyph;
+        e[5] += -(cp2 / wphi(p, 5)) *
+                (Nphi + (p->beta1 - 1.0) * vy * dxph + (p->beta2 - 1.0) * vx * dyph);
+      } else {
+        n[1] += -(cp2 / wphi(p, 1)) * dxph;
+        n[2] += -(cp2 / wphi(p, 2)) * dyph;
+        n[5] += -(cp2 / wphi(p, 5)) * (Nphi + p->beta1 * vy * dxph + p->beta2 * vx * dyph);
+      }
     }
     matvec(TI_, m, fl);
-    matvec(TI_, n, gl);
+    if (central) {
+      double C[Q * Q];
+      central_matrix(vx, vy, C);
+      solve9(C, e, gl);
+    } else {
+      matvec(TI_, n, gl);
+    }
     for (int a = 0; a < Q; ++a) {
       f[a * N + c] = emulate(p, fl[a], w[a] * p->rho0, p->scale_f);
       g[a * N + c] = emulate(p, gl[a], wp[a] * p->phi0, p->scale_g);
@@ -392,13 +567,23 @@ void orc_fields(const orc_params* p, const double* f, const double* g, double* o
     double n1 = n[1] - phi * ux, n2 = n[2] - phi * uy;
     double n5 = n[5] - phi * ux * uy;
     /* scalar gradient from the first-order non-equilibrium moments */
-    double dxph = -p->lam_phi[1] / cp2 * n1;
-    double dyph = -p->lam_phi[2] / cp2 * n2;
+    double dxph = -wphi(p, 1) / cp2 * n1;
+    double dyph = -wphi(p, 2) / cp2 * n2;
     /* N_xy and N^phi_xy, Eqs. (crossderivativeRHS1), (crossderivativeRHS2) */
     double Nxy = -p->lam[5] / (rho * cs2) * m5;
     double dxuy = NAN, dyux = NAN, om = NAN, Nph = NAN;
     if (fabs(phi) >= p->phi_min) {
-      Nph = -p->lam_phi[5] / (phi * cp2) * n5 - (b1 * uy * dxph + b2 * ux * dyph) / phi;
+      if (p->scalar_model >= 2) {
+        /* central-moment models (reading, see orc_init): the central xy moment,
+         * whose equilibrium is zero, with (beta - 1) in the correction term */
+        double C[Q * Q], k[Q];
+        central_matrix(ux, uy, C);
+        matvec(C, gl, k);
+        Nph = -wphi(p, 5) / (phi * cp2) * k[5] -
+              ((b1 - 1.0) * uy * dxph + (b2 - 1.0) * ux * dyph) / phi;
+      } else {
+        Nph = -wphi(p, 5) / (phi * cp2) * n5 - (b1 * uy * dxph + b2 * ux * dyph) / phi;
+      }
       dxuy = (Nph - b2 * Nxy) / (b1 - b2);      /* Eq. (offdiagvelderivativeresult1) */
       dyux = (b1 * Nxy - Nph) / (b1 - b2);      /* Eq. (offdiagvelderivativeresult2) */
       om = (2.0 * Nph - (b1 + b2) * Nxy) / (b1 - b2); /* Eq. (vorticityexpression) */
