@@ -38,6 +38,8 @@ def parse():
     ap.add_argument("--n", type=int, default=16384, help="grid side of the Taylor-Green lattice")
     ap.add_argument("--lb-steps", type=int, default=200, help="fused time steps per benchmark step")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--scalar-model", default="mrt", choices=["mrt", "srt", "cascaded", "central"],
+                    help="scalar collision (Sec. 3 MRT, App. B SRT, App. C cascaded, App. D central)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="tg", choices=["tg", "batch", "cavity", "surrogate"],
@@ -149,7 +151,8 @@ def rates(nu):
 
 
 def workload_name(args):
-    return (f"taylor-green {args.n}x{args.n}, D2Q9 flow + scalar, {args.storage} storage, "
+    model = "" if args.scalar_model == "mrt" else f" ({args.scalar_model} scalar collision)"
+    return (f"taylor-green {args.n}x{args.n}, D2Q9 flow + scalar{model}, {args.storage} storage, "
             f"{args.lb_steps} fused steps + local S/omega fields per benchmark step")
 
 
@@ -216,7 +219,8 @@ def traffic_per_launch(args, n_cells):
         with open(path) as f:
             d = json.load(f)
         import hashlib
-        e = d.get(f"k_step_{args.storage}")
+        e = d.get(f"k_step_{args.storage}" + ("" if args.scalar_model == "mrt" else
+                                               f"_{args.scalar_model}"))
         if not e:
             return None
         h = hashlib.sha256()
@@ -244,7 +248,7 @@ def run_ours(args, world, rank, local):
     cfg = D.Config(nx=n, ny=n, storage=args.storage, omega_f=wf, omega_g=wg,
                    scale_f=2.0 ** 10 if args.storage == "fp16" else 0.0,
                    scale_g=2.0 ** 10 if args.storage == "fp16" else 0.0,
-                   host_io=not args.no_e2e)
+                   host_io=not args.no_e2e, scalar_model=args.scalar_model)
     stream = torch.cuda.Stream(dev)
     with torch.cuda.stream(stream):
         lat = D.Lattice(cfg, device=dev, stream=stream)

@@ -64,6 +64,26 @@ typedef enum {
  * scale_g; collision arithmetic is always FP32. */
 typedef enum { DDFLB_FP32 = 0, DDFLB_FP16 = 1, DDFLB_BF16 = 2 } ddflb_storage;
 
+/* Collision model of the scalar lattice.  MRT: Sec. 3 (raw moments, rates
+ * omega_g).  SRT: App. B, g~ = g - (g - g^eq)/tau_phi with 1/tau_phi =
+ * omega_g[1] (entries 2..8 are ignored; run as the MRT with all rates equal,
+ * which is the same collision).  CASCADED: App. C, central moments relaxed at
+ * the rates omega_g through the cascade of moment changes h_1..h_8 in the
+ * orthogonal basis K (K6, K7 read as 2|e_y> - 3|e_x^2 e_y>, 2|e_x> - 3|e_x e_y^2>,
+ * the orthogonal forms the paper's inner products require).  CENTRAL: App. D,
+ * central moments relaxed directly (raw -> central -> relax -> raw).  For the
+ * two central-moment models the equilibria are Eq. (eqmcentralmoment_CDE) and
+ * omega is recovered from the central xy non-equilibrium moment with
+ * (beta - 1) in the scalar-gradient correction (the Chapman-Enskog expansion
+ * of a central-moment collision; the paper does not write it out).  The
+ * batched entry points accept MRT and SRT only. */
+typedef enum {
+  DDFLB_SCALAR_MRT = 0,
+  DDFLB_SCALAR_SRT = 1,
+  DDFLB_SCALAR_CASCADED = 2,
+  DDFLB_SCALAR_CENTRAL = 3
+} ddflb_scalar_model;
+
 /* ddflb_params.flags */
 #define DDFLB_FLAG_HOST_IO 1 /* reserve a staging area so ddflb_init_host /
                                 ddflb_fields_host can take host buffers */
@@ -101,6 +121,10 @@ typedef struct {
    * points and ddflb_reduce_noalloc accept only fx = fy = force_omega = 0. */
   double fx, fy;
   double force_omega;
+  /* Scalar collision model (ddflb_scalar_model).  The local kinematics of
+   * Sec. 4 are evaluated to match it. */
+  int32_t scalar_model;
+  int32_t reserved;     /* must be 0 */
 } ddflb_params;
 
 typedef struct ddflb_ctx ddflb_ctx;

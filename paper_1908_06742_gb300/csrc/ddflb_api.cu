@@ -96,6 +96,9 @@ ddflb_status validate(const ddflb_params* p) {
   if (p->check_every < 0) return fail(DDFLB_EINVAL, "check_every < 0");
   if (!std::isfinite(p->fx) || !std::isfinite(p->fy) || !std::isfinite(p->force_omega))
     return fail(DDFLB_EINVAL, "non-finite body force or force frequency");
+  if (p->scalar_model < 0 || p->scalar_model > 3)
+    return fail(DDFLB_EINVAL, "scalar_model %d is not a ddflb_scalar_model", p->scalar_model);
+  if (p->reserved != 0) return fail(DDFLB_EINVAL, "reserved must be 0");
   for (double s : {p->scale_f, p->scale_g}) {
     if (s > 0) {
       int e;
@@ -113,8 +116,11 @@ LbParams make_lb(const ddflb_params* p, int pitch) {
   P.plane = (int64_t)pitch * p->ny;
   for (int k = 0; k < 9; ++k) {
     P.wf[k] = (float)p->omega_f[k];
-    P.wg[k] = (float)p->omega_g[k];
+    // SRT (App. B): one rate for every non-conserved scalar moment
+    const double wg = p->scalar_model == DDFLB_SCALAR_SRT && k > 0 ? p->omega_g[1] : p->omega_g[k];
+    P.wg[k] = (float)wg;
   }
+  P.smodel = p->scalar_model;
   P.b1 = (float)p->beta1;
   P.b2 = (float)p->beta2;
   P.inv_db = (float)(1.0 / (p->beta1 - p->beta2));
@@ -296,7 +302,7 @@ ddflb_status ddflb_init(ddflb_ctx* c, const float* rho, const float* ux, const f
   if (!c || !rho || !ux || !uy || !phi) return fail(DDFLB_EINVAL, "NULL handle or field");
   if (grads) {
     const double* wf = c->p.omega_f;
-    const double* wg = c->p.omega_g;
+    const float* wg = c->L.P.wg;
     if (wf[3] <= 0 || wf[4] <= 0 || wf[5] <= 0 || wg[1] <= 0 || wg[2] <= 0 || wg[5] <= 0)
       return fail(DDFLB_EINVAL, "gradient initialisation needs w3, w4, w5, w1^phi, w2^phi, "
                                 "w5^phi > 0");

@@ -498,6 +498,10 @@ size_t ddflb_batch_workspace_bytes(int32_t n, const ddflb_params* p) {
   if (n <= 0 || !p) return 0;
   for (int i = 0; i < n; ++i) {
     if (ddflb_workspace_bytes(&p[i]) == 0) return 0;
+    if (p[i].scalar_model >= DDFLB_SCALAR_CASCADED) {
+      set_error("the batched step runs the MRT and SRT scalar collisions only");
+      return 0;
+    }
     if (p[i].fx != 0.0 || p[i].fy != 0.0 || p[i].force_omega != 0.0) {
       set_error("the batched step runs unforced instances only (fx = fy = force_omega = 0)");
       return 0;

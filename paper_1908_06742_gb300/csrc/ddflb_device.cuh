@@ -48,6 +48,8 @@ struct LbParams {
   // body force (Sec. 2): F = (fx + field_x, fy + field_y) * fmod at every node
   float fx, fy, fmod;
   const float* ffield;    // optional [2][ny][nx] (row stride nx), or null
+  int smodel;             // scalar collision: 0 MRT, 1 SRT (MRT with equal rates),
+                          // 2 cascaded (App. C), 3 central moments (App. D)
 };
 
 // Device status block (one per lattice pair), written by the reductions.
@@ -372,9 +374,108 @@ __device__ __forceinline__ void relax_source(const float w[9], const Neq& n, con
   d[8] -= 0.25f * (r - s2);
 }
 
+// ------------------------------------------------------------ central-moment scalar models
+// Non-equilibrium central moments nu = eta - eta^eq of the scalar lattice
+// (Eq. centralmomentdefinitions_CDE, equilibria Eq. eqmcentralmoment_CDE),
+// formed from the raw non-equilibrium moments n of neq_scalar by the binomial
+// shift by u.  The raw image of the central equilibria equals the raw
+// equilibria of Eq. (eqmrawmoment_CDE) up to third order; in the fourth-order
+// moment it is larger by 2 c phi ((b2 - 1) ux^2 + (b1 - 1) uy^2).
+struct CNeq {
+  float x, y, xx, yy, xy, xxy, xyy, xxyy;
+};
+
+__device__ __forceinline__ CNeq central_neq(const LbParams& P, const Neq& n, const Macro& q) {
+  const float c = 1.0f / 3.0f, ux = q.ux, uy = q.uy;
+  const float rx = n.n1, ry = n.n2, rxx = 0.5f * (n.n3 + n.n4), ryy = 0.5f * (n.n3 - n.n4);
+  const float rxy = n.n5, rxxy = n.n6, rxyy = n.n7;
+  const float rxxyy = n.n8 - 2.0f * c * q.phi * ((P.b2 - 1.0f) * ux * ux + (P.b1 - 1.0f) * uy * uy);
+  CNeq v;
+  v.x = rx;
+  v.y = ry;
+  v.xx = rxx - 2.0f * ux * rx;
+  v.yy = ryy - 2.0f * uy * ry;
+  v.xy = rxy - uy * rx - ux * ry;
+  v.xxy = rxxy - 2.0f * ux * rxy + ux * ux * ry - uy * rxx + 2.0f * ux * uy * rx;
+  v.xyy = rxyy - 2.0f * uy * rxy + uy * uy * rx - ux * ryy + 2.0f * ux * uy * ry;
+  v.xxyy = rxxyy - 2.0f * ux * rxyy - 2.0f * uy * rxxy + ux * ux * ryy + uy * uy * rxx +
+           4.0f * ux * uy * rxy - 2.0f * ux * ux * uy * ry - 2.0f * ux * uy * uy * rx;
+  return v;
+}
+
+// App. D (non-cascaded): each central moment relaxes at its own rate (xx + yy at
+// w3, xx - yy at w4); the change is taken back to raw moments by the inverse
+// binomial shift and to populations by the inverse of App. B, and added to d.
+__device__ __forceinline__ void relax_central(const float w[9], const CNeq& v, const Macro& q,
+                                              float d[9]) {
+  const float ux = q.ux, uy = q.uy;
+  const float Dx = -w[1] * v.x, Dy = -w[2] * v.y;
+  const float Ds = -w[3] * (v.xx + v.yy), Dd = -w[4] * (v.xx - v.yy);
+  const float Dxx = 0.5f * (Ds + Dd), Dyy = 0.5f * (Ds - Dd);
+  const float Dxy = -w[5] * v.xy, Dxxy = -w[6] * v.xxy, Dxyy = -w[7] * v.xyy;
+  const float Dxxyy = -w[8] * v.xxyy;
+  const float Rxx = Dxx + 2.0f * ux * Dx, Ryy = Dyy + 2.0f * uy * Dy;
+  const float Rxy = Dxy + uy * Dx + ux * Dy;
+  const float Rxxy = Dxxy + 2.0f * ux * Dxy + ux * ux * Dy + uy * Dxx + 2.0f * ux * uy * Dx;
+  const float Rxyy = Dxyy + 2.0f * uy * Dxy + uy * uy * Dx + ux * Dyy + 2.0f * ux * uy * Dy;
+  const float Rxxyy = Dxxyy + 2.0f * ux * Dxyy + 2.0f * uy * Dxxy + ux * ux * Dyy + uy * uy * Dxx +
+                      4.0f * ux * uy * Dxy + 2.0f * ux * ux * uy * Dy + 2.0f * ux * uy * uy * Dx;
+  float dd[9];
+  populations(0.0f, Dx, Dy, Rxx + Ryy, Rxx - Ryy, Rxy, Rxxy, Rxyy, Rxxyy, dd);
+#pragma unroll
+  for (int a = 0; a < 9; ++a) d[a] += dd[a];
+}
+
+// App. C (cascaded): the changes h1..h8 in the orthogonal basis K, found order by
+// order so that every central moment relaxes at its rate; g~ = g + K h.  K6 and
+// K7 are the orthogonal 2|e_y> - 3|e_x^2 e_y>, 2|e_x> - 3|e_x e_y^2> (the forms
+// the paper's inner products and expansion of g~ require).
+__device__ __forceinline__ void relax_cascaded(const float w[9], const CNeq& v, const Macro& q,
+                                               float d[9]) {
+  const float ux = q.ux, uy = q.uy, ux2 = ux * ux, uy2 = uy * uy;
+  const float h1 = -w[1] * v.x * (1.0f / 6.0f);
+  const float h2 = -w[2] * v.y * (1.0f / 6.0f);
+  const float h3 = -w[3] * (v.xx + v.yy) * (1.0f / 12.0f) + (ux * h1 + uy * h2);
+  const float h4 = -w[4] * (v.xx - v.yy) * 0.25f + 3.0f * (ux * h1 - uy * h2);
+  const float h5 = -w[5] * v.xy * 0.25f + 1.5f * (ux * h2 + uy * h1);
+  const float h6 = w[6] * v.xxy * 0.25f - 2.0f * ux * h5 - 0.5f * uy * h4 - 1.5f * uy * h3 +
+                   (1.0f + 1.5f * ux2) * h2 + 3.0f * ux * uy * h1;
+  const float h7 = w[7] * v.xyy * 0.25f - 2.0f * uy * h5 + 0.5f * ux * h4 - 1.5f * ux * h3 +
+                   3.0f * ux * uy * h2 + (1.0f + 1.5f * uy2) * h1;
+  const float h8 = -w[8] * v.xxyy * 0.25f - 2.0f * ux * h7 - 2.0f * uy * h6 -
+                   4.0f * ux * uy * h5 + 0.5f * (ux2 - uy2) * h4 -
+                   (2.0f + 1.5f * (ux2 + uy2)) * h3 + (2.0f + 3.0f * ux2) * uy * h2 +
+                   (2.0f + 3.0f * uy2) * ux * h1;
+  constexpr int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+  constexpr int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    const float x = (float)ex[a], y = (float)ey[a], x2 = x * x, y2 = y * y;
+    d[a] += x * h1 + y * h2 + (3.0f * (x2 + y2) - 4.0f) * h3 + (x2 - y2) * h4 + x * y * h5 +
+            (2.0f * y - 3.0f * x2 * y) * h6 + (2.0f * x - 3.0f * x * y2) * h7 +
+            (9.0f * x2 * y2 - 6.0f * (x2 + y2) + 4.0f) * h8;
+  }
+}
+
+// Scalar collision of the model SM (0: the MRT of Sec. 3, also used for the
+// SRT with equal rates; 2 cascaded; 3 central moments).
+template <int SM>
+__device__ __forceinline__ void collide_scalar(const LbParams& P, const Mom& mg, const Mom& mf,
+                                               const Macro& q, float dg[9]) {
+  if (SM == 0) {
+    relax(P.wg, neq_scalar(P, mg, mf, q), dg);
+  } else {
+    const CNeq v = central_neq(P, neq_scalar(P, mg, mf, q), q);
+    if (SM == 2)
+      relax_cascaded(P.wg, v, q, dg);
+    else
+      relax_central(P.wg, v, q, dg);
+  }
+}
+
 // Moments, macroscopic state and both collisions of one node, in place on the
 // pulled deviations df, dg.  FORCE = false is the unforced step.
-template <bool FORCE>
+template <bool FORCE, int SM = 0>
 __device__ __forceinline__ void collide(const LbParams& P, int x, int y, float df[9],
                                         float dg[9]) {
   Mom mf = moments_flow(df);
@@ -383,11 +484,11 @@ __device__ __forceinline__ void collide(const LbParams& P, int x, int y, float d
     const Force F = node_force(P, x, y);
     const Macro q = macro_force(P, mf, mg, F);
     relax_source(P.wf, neq_flow(mf, q), source(F, q), df);
-    relax(P.wg, neq_scalar(P, mg, mf, q), dg);
+    collide_scalar<SM>(P, mg, mf, q, dg);
   } else {
     const Macro q = macro(P, mf, mg);
     relax(P.wf, neq_flow(mf, q), df);
-    relax(P.wg, neq_scalar(P, mg, mf, q), dg);
+    collide_scalar<SM>(P, mg, mf, q, dg);
   }
 }
 
@@ -448,7 +549,12 @@ __device__ __forceinline__ Kin kinematics(const LbParams& P, const Neq& nf, cons
   k.dyphi = dyphi;
   if (fabsf(q.phi) >= P.phimin) {
     const float iphi = __frcp_rn(q.phi);
-    const float Nphi = (-P.wg[5] * ng.n5 * inv_c - (P.b1 * q.uy * dxphi + P.b2 * q.ux * dyphi)) * iphi;
+    // central-moment models: the central xy moment (equilibrium zero) and
+    // (beta - 1) in the scalar-gradient correction
+    const bool cm = P.smodel >= 2;
+    const float n5 = cm ? ng.n5 - q.uy * ng.n1 - q.ux * ng.n2 : ng.n5;
+    const float c1 = cm ? P.b1 - 1.0f : P.b1, c2 = cm ? P.b2 - 1.0f : P.b2;
+    const float Nphi = (-P.wg[5] * n5 * inv_c - (c1 * q.uy * dxphi + c2 * q.ux * dyphi)) * iphi;
     k.omega = (2.0f * Nphi - (P.b1 + P.b2) * N) * P.inv_db;
     k.dxuy = (Nphi - P.b2 * N) * P.inv_db;
     k.dyux = (P.b1 * N - Nphi) * P.inv_db;

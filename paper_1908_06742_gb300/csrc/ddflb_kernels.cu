@@ -21,7 +21,7 @@
 namespace ddflb {
 
 // ------------------------------------------------------------------ step
-template <typename S, int BC, bool FORCE>
+template <typename S, int BC, bool FORCE, int SM>
 __global__ void __launch_bounds__(256) k_step(LbParams P, const S* __restrict__ fin,
                                               const S* __restrict__ gin, S* __restrict__ fout,
                                               S* __restrict__ gout,
@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(256) k_step(LbParams P, const S* __restrict__ 
   if (status != nullptr && status->diverged) return;
   float df[9], dg[9];
   pull<S, BC>(P, fin, gin, x, y, df, dg);
-  collide<FORCE>(P, x, y, df, dg);
+  collide<FORCE, SM>(P, x, y, df, dg);
   const int64_t o = (int64_t)y * P.pitch + x;
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
@@ -108,6 +108,12 @@ __global__ void __launch_bounds__(256) k_init(LbParams P, InitPtrs in, S* __rest
   // equilibrium moments, Eqs. (eqmrawmoment), (eqmrawmoment_CDE), deviation form
   float m3 = 2.0f * c * k0 + rho * usq, m4 = rho * (uxx - uyy), m5 = jx * uy;
   float e1 = px, e2 = py, e3 = 2.0f * c * n0 + phi * usq, e4 = phi * (uxx - uyy), e5 = px * uy;
+  float e6 = py * (P.b1 * c + uxx), e7 = px * (P.b2 * c + uyy);
+  float e8 = c * c * n0 + phi * (c * usq + uxx * uyy);
+  const bool cm = P.smodel >= 2;  // central-moment scalar models (Apps. C, D)
+  // their equilibrium is the raw image of the central equilibria: larger in
+  // the fourth-order moment by 2 c phi ((b2 - 1) ux^2 + (b1 - 1) uy^2)
+  if (cm) e8 += 2.0f * c * phi * ((P.b2 - 1.0f) * uxx + (P.b1 - 1.0f) * uyy);
   if (in.grads) {
     // Chapman-Enskog non-equilibrium parts: Eqs. (strainratexxpyy)-(strainratexy)
     // for the flow; Eqs. (1stnoneqmmomentx_CDE), (1stnoneqmmomenty_CDE),
@@ -118,9 +124,27 @@ __global__ void __launch_bounds__(256) k_init(LbParams P, InitPtrs in, S* __rest
     m3 += -2.0f * c * rho / P.wf[3] * (dxux + dyuy);
     m4 += -2.0f * c * rho / P.wf[4] * (dxux - dyuy);
     m5 += -c * rho / P.wf[5] * (dxuy + dyux);
-    e1 += -c / P.wg[1] * dxph;
-    e2 += -c / P.wg[2] * dyph;
-    e5 += -c / P.wg[5] * (phi * (P.b1 * dxuy + P.b2 * dyux) + P.b1 * uy * dxph + P.b2 * ux * dyph);
+    const float Nphi = phi * (P.b1 * dxuy + P.b2 * dyux);
+    const float vx = -c / P.wg[1] * dxph, vy = -c / P.wg[2] * dyph;
+    if (!cm) {
+      e1 += vx;
+      e2 += vy;
+      e5 += -c / P.wg[5] * (Nphi + P.b1 * uy * dxph + P.b2 * ux * dyph);
+    } else {
+      // central non-equilibrium parts (x, y and xy), taken to raw moments by the
+      // inverse binomial shift: eta_xy^(1) = -(c / w5)[phi N^phi + (b1 - 1) uy
+      // dxphi + (b2 - 1) ux dyphi]
+      const float vxy =
+          -c / P.wg[5] * (Nphi + (P.b1 - 1.0f) * uy * dxph + (P.b2 - 1.0f) * ux * dyph);
+      e1 += vx;
+      e2 += vy;
+      e3 += 2.0f * (ux * vx + uy * vy);
+      e4 += 2.0f * (ux * vx - uy * vy);
+      e5 += vxy + uy * vx + ux * vy;
+      e6 += 2.0f * ux * vxy + uxx * vy + 2.0f * ux * uy * vx;
+      e7 += 2.0f * uy * vxy + uyy * vx + 2.0f * ux * uy * vy;
+      e8 += 2.0f * uxx * uy * vy + 2.0f * ux * uyy * vx + 4.0f * ux * uy * vxy;
+    }
   }
   float m1 = jx, m2 = jy, m6 = jy * (c + uxx), m7 = jx * (c + uyy);
   float m8 = c * c * k0 + rho * (c * usq + uxx * uyy);
@@ -139,8 +163,7 @@ __global__ void __launch_bounds__(256) k_init(LbParams P, InitPtrs in, S* __rest
   }
   float df[9], dg[9];
   populations(k0, m1, m2, m3, m4, m5, m6, m7, m8, df);
-  populations(n0, e1, e2, e3, e4, e5, py * (P.b1 * c + uxx), px * (P.b2 * c + uyy),
-              c * c * n0 + phi * (c * usq + uxx * uyy), dg);
+  populations(n0, e1, e2, e3, e4, e5, e6, e7, e8, dg);
   constexpr int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
   constexpr int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
   constexpr int opp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
@@ -256,7 +279,7 @@ dim3 grid2d(const LbParams& P, dim3 b) {
   return dim3((P.nx + b.x - 1) / b.x, (P.ny + b.y - 1) / b.y);
 }
 
-template <typename S, int BC, bool FORCE>
+template <typename S, int BC, bool FORCE, int SM>
 cudaError_t run(const Launch& L, int what, const void* fin, const void* gin, void* a, void* b,
                 const FieldPtrs* fp, const InitPtrs* ip, int mode, double* partials, int nparts,
                 const DevStatus* st) {
@@ -277,18 +300,31 @@ cudaError_t run(const Launch& L, int what, const void* fin, const void* gin, voi
           L.P, (const S*)fin, (const S*)gin, (float*)a, mode, partials);
       break;
     default:
-      k_step<S, BC, FORCE><<<g, blk, 0, L.stream>>>(L.P, (const S*)fin, (const S*)gin, (S*)a,
-                                                    (S*)b, st);
+      k_step<S, BC, FORCE, SM><<<g, blk, 0, L.stream>>>(L.P, (const S*)fin, (const S*)gin,
+                                                        (S*)a, (S*)b, st);
   }
   return cudaGetLastError();
+}
+
+// scalar model: the step kernel is specialised (0 MRT / SRT, 2 cascaded, 3 central
+// moments); the other kernels read P.smodel where it matters
+template <typename S, int BC, bool FORCE>
+cudaError_t run_sm(const Launch& L, int what, const void* fin, const void* gin, void* a, void* b,
+                   const FieldPtrs* fp, const InitPtrs* ip, int mode, double* partials, int np,
+                   const DevStatus* st) {
+  if (what != 4 || L.P.smodel < 2)
+    return run<S, BC, FORCE, 0>(L, what, fin, gin, a, b, fp, ip, mode, partials, np, st);
+  if (L.P.smodel == 2)
+    return run<S, BC, FORCE, 2>(L, what, fin, gin, a, b, fp, ip, mode, partials, np, st);
+  return run<S, BC, FORCE, 3>(L, what, fin, gin, a, b, fp, ip, mode, partials, np, st);
 }
 
 template <typename S, int BC>
 cudaError_t run_f(const Launch& L, int what, const void* fin, const void* gin, void* a, void* b,
                   const FieldPtrs* fp, const InitPtrs* ip, int mode, double* partials, int np,
                   const DevStatus* st) {
-  if (L.force) return run<S, BC, true>(L, what, fin, gin, a, b, fp, ip, mode, partials, np, st);
-  return run<S, BC, false>(L, what, fin, gin, a, b, fp, ip, mode, partials, np, st);
+  if (L.force) return run_sm<S, BC, true>(L, what, fin, gin, a, b, fp, ip, mode, partials, np, st);
+  return run_sm<S, BC, false>(L, what, fin, gin, a, b, fp, ip, mode, partials, np, st);
 }
 
 template <typename S>

@@ -183,7 +183,8 @@ cudaError_t go_bc(const Launch& L, const void* fin, const void* gin, void* fout,
 }  // namespace
 
 bool pair_step_eligible(const Launch& L) {
-  return !L.force && L.storage != 0 && L.P.nx % 2 == 0 && L.block.x % 32 == 0;
+  return !L.force && L.P.smodel < 2 && L.storage != 0 && L.P.nx % 2 == 0 &&
+         L.block.x % 32 == 0;
 }
 
 cudaError_t launch_step_pair(const Launch& L, const void* fin, const void* gin, void* fout,

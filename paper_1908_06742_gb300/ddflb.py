@@ -21,6 +21,7 @@ OK, EINVAL, ENOMEM, ECUDA, EDIVERGED, ENOTCONVERGED, ETIMEOUT = range(7)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EDIVERGED", "ENOTCONVERGED", "ETIMEOUT"]
 BC = {"periodic": 0, "cavity": 1, "channel": 2}
 STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
+SCALAR_MODEL = {"mrt": 0, "srt": 1, "cascaded": 2, "central": 3}
 FLAG_HOST_IO = 1
 FIELD_NAMES = ("rho", "ux", "uy", "phi", "sxx", "sxy", "syy", "omega")
 DERIVED_NAMES = ("dxux", "dyux", "dxuy", "dyuy", "dxphi", "dyphi", "q", "r", "lamb_x", "lamb_y")
@@ -46,6 +47,7 @@ class Params(ctypes.Structure):
         ("scale_f", ctypes.c_double), ("scale_g", ctypes.c_double),
         ("check_every", ctypes.c_int32), ("flags", ctypes.c_int32),
         ("fx", ctypes.c_double), ("fy", ctypes.c_double), ("force_omega", ctypes.c_double),
+        ("scalar_model", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 
@@ -179,6 +181,7 @@ class Config:
     host_io: bool = False
     omega_f: Optional[tuple] = None   # explicit 9-entry diagonals override the above
     omega_g: Optional[tuple] = None
+    scalar_model: str = "mrt"   # "mrt" (Sec. 3), "srt" (App. B), "cascaded" (App. C), "central" (App. D)
     fx: float = 0.0             # body force (Sec. 2), times cos(force_omega t)
     fy: float = 0.0
     force_omega: float = 0.0
@@ -209,6 +212,7 @@ class Config:
         p.check_every = self.check_every
         p.flags = FLAG_HOST_IO if self.host_io else 0
         p.fx, p.fy, p.force_omega = self.fx, self.fy, self.force_omega
+        p.scalar_model = SCALAR_MODEL[self.scalar_model]
         return p
 
 
