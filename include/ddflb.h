@@ -152,10 +152,12 @@ ddflb_status ddflb_create(const ddflb_params* p, void* dev_workspace, size_t byt
 ddflb_status ddflb_init(ddflb_ctx* c, const float* rho, const float* ux, const float* uy,
                         const float* phi, const float* grads);
 
-/* ddflb_init with HOST input buffers (same layout); the copies run on the
- * context stream through the staging area, so the host buffers must stay
- * valid until the stream reaches this point (pinned memory for overlap).
- * Requires DDFLB_FLAG_HOST_IO at creation (else EINVAL). */
+/* ddflb_init with HOST input buffers (same layout); the copies run through
+ * the input staging area, on the context stream or, after ddflb_set_io_stream,
+ * on the I/O stream.  The call does not wait for them: the host buffers must
+ * stay valid and unchanged until they are done (ddflb_io_wait, or a
+ * synchronisation of the stream that ran them); pinned memory lets the copies
+ * overlap with compute.  Requires DDFLB_FLAG_HOST_IO at creation (else EINVAL). */
 ddflb_status ddflb_init_host(ddflb_ctx* c, const float* rho, const float* ux, const float* uy,
                              const float* phi, const float* grads);
 
@@ -195,10 +197,31 @@ ddflb_status ddflb_derived(ddflb_ctx* c, float* dxux, float* dyux, float* dxuy, 
                            float* lamb_y);
 
 /* ddflb_fields into HOST buffers (staged; requires DDFLB_FLAG_HOST_IO).  The
- * copies are queued on the context stream; the call synchronises it before
- * returning so the host buffers hold the result. */
+ * call waits until the host buffers hold the result (ddflb_fields_host_async
+ * followed by ddflb_io_wait). */
 ddflb_status ddflb_fields_host(ddflb_ctx* c, float* rho, float* ux, float* uy, float* phi,
                                float* sxx, float* sxy, float* syy, float* omega);
+
+/* ddflb_fields into HOST buffers without waiting: the fields kernel writes the
+ * output staging area on the context stream and the copies to the host run on
+ * the I/O stream (or the context stream); the host buffers hold the result
+ * after ddflb_io_wait.  The next ddflb_fields_host_async waits on the device
+ * for these copies before it reuses the staging area. */
+ddflb_status ddflb_fields_host_async(ddflb_ctx* c, float* rho, float* ux, float* uy, float* phi,
+                                     float* sxx, float* sxy, float* syy, float* omega);
+
+/* Run the host<->device copies of ddflb_init_host / ddflb_fields_host_async on
+ * io_stream (a cudaStream_t of the context's device; NULL: back to the context
+ * stream), so they overlap with the time steps.  Ordering against the compute
+ * stream is kept with events: an upload waits until the previous ddflb_init
+ * has consumed the input staging area, ddflb_init waits for its upload, a
+ * download waits for its fields kernel, and the next fields kernel waits for
+ * the previous download.  This is host-side pipelining only (no paper
+ * counterpart).  Requires DDFLB_FLAG_HOST_IO. */
+ddflb_status ddflb_set_io_stream(ddflb_ctx* c, void* io_stream);
+
+/* Wait until every host copy queued by this context has completed. */
+ddflb_status ddflb_io_wait(ddflb_ctx* c);
 
 /* The pre-collision populations of the current state as full values (not
  * deviations), f and g each [9][ny][nx] device floats (either may be NULL). */

@@ -44,7 +44,7 @@ size_t elem_size(int storage) { return storage == DDFLB_FP32 ? 4 : 2; }
 struct Layout {
   int pitch;
   size_t pops_bytes;  // one buffer: 2 lattices x 9 planes
-  size_t off_a, off_b, off_uprev, off_part, off_status, off_stage, total;
+  size_t off_a, off_b, off_uprev, off_part, off_status, off_stage, off_stage_out, total;
 };
 
 // Row pitch: a multiple of 64 elements keeps every row start 128-byte aligned
@@ -61,8 +61,10 @@ Layout layout(const ddflb_params* p) {
   L.off_uprev = o; o += align_up(2 * cells * sizeof(float), kAlign);
   L.off_part = o; o += align_up((size_t)kReduceBlocks * 4 * sizeof(double), kAlign);
   L.off_status = o; o += align_up(sizeof(DevStatus), kAlign);
-  L.off_stage = o;
+  L.off_stage = o;  // host I/O: 10 input planes, then 8 output planes
   if (p->flags & DDFLB_FLAG_HOST_IO) o += align_up(10 * cells * sizeof(float), kAlign);
+  L.off_stage_out = o;
+  if (p->flags & DDFLB_FLAG_HOST_IO) o += align_up(8 * cells * sizeof(float), kAlign);
   L.total = o;
   return L;
 }
@@ -180,6 +182,9 @@ struct ddflb_ctx {
   int64_t step;
   int64_t snap_step;  // step at which uprev was last written (-1: none)
   int path;           // step kernel: 0 / 1 one node per thread, 2 paired nodes (16-bit storage)
+  float* stage_out;   // output staging area (host I/O)
+  cudaStream_t io;    // stream of the host copies (null: the context stream)
+  cudaEvent_t ev_in_free, ev_in_ready, ev_out_ready, ev_out_free;  // host-I/O ordering
 };
 
 namespace {
@@ -280,6 +285,7 @@ ddflb_status ddflb_create(const ddflb_params* p, void* ws, size_t bytes, void* s
   c->partials = (double*)(c->ws + lay.off_part);
   c->status = (DevStatus*)(c->ws + lay.off_status);
   c->stage = (p->flags & DDFLB_FLAG_HOST_IO) ? (float*)(c->ws + lay.off_stage) : nullptr;
+  c->stage_out = (p->flags & DDFLB_FLAG_HOST_IO) ? (float*)(c->ws + lay.off_stage_out) : nullptr;
   c->L.P = make_lb(p, lay.pitch);
   c->L.P_bc = p->bc;
   c->L.storage = p->storage;
@@ -321,6 +327,15 @@ ddflb_status ddflb_init(ddflb_ctx* c, const float* rho, const float* ux, const f
   return checks_at(c);
 }
 
+// Host-I/O ordering between the copy stream and the compute stream (no-ops when
+// the copies run on the compute stream itself).
+static cudaError_t io_order(ddflb_ctx* c, cudaStream_t waiter, cudaEvent_t ev,
+                            cudaStream_t recorder) {
+  if (!c->io) return cudaSuccess;
+  cudaError_t e = cudaEventRecord(ev, recorder);
+  return e == cudaSuccess ? cudaStreamWaitEvent(waiter, ev, 0) : e;
+}
+
 ddflb_status ddflb_init_host(ddflb_ctx* c, const float* rho, const float* ux, const float* uy,
                              const float* phi, const float* grads) {
   if (!c || !rho || !ux || !uy || !phi) return fail(DDFLB_EINVAL, "NULL handle or field");
@@ -329,16 +344,24 @@ ddflb_status ddflb_init_host(ddflb_ctx* c, const float* rho, const float* ux, co
   const float* src[5] = {rho, ux, uy, phi, grads};
   const size_t planes[5] = {1, 1, 1, 1, 6};
   float* dst[5];
+  cudaStream_t cs = c->io ? c->io : c->L.stream;
+  // the upload waits until the previous init has read the staging area
+  cudaError_t e = c->io ? cudaStreamWaitEvent(cs, c->ev_in_free, 0) : cudaSuccess;
+  if (e != cudaSuccess) return cuda_fail(e, "init_host order");
   size_t o = 0;
   for (int k = 0; k < 5; ++k) {
     dst[k] = c->stage + o * n;
     o += planes[k];
     if (!src[k]) continue;
-    cudaError_t e = cudaMemcpyAsync(dst[k], src[k], planes[k] * n * sizeof(float),
-                                    cudaMemcpyHostToDevice, c->L.stream);
+    e = cudaMemcpyAsync(dst[k], src[k], planes[k] * n * sizeof(float), cudaMemcpyHostToDevice, cs);
     if (e != cudaSuccess) return cuda_fail(e, "init_host copy");
   }
-  return ddflb_init(c, dst[0], dst[1], dst[2], dst[3], grads ? dst[4] : nullptr);
+  e = io_order(c, c->L.stream, c->ev_in_ready, cs);
+  if (e != cudaSuccess) return cuda_fail(e, "init_host order");
+  ddflb_status s = ddflb_init(c, dst[0], dst[1], dst[2], dst[3], grads ? dst[4] : nullptr);
+  if (s != DDFLB_OK) return s;
+  e = c->io ? cudaEventRecord(c->ev_in_free, c->L.stream) : cudaSuccess;
+  return e == cudaSuccess ? DDFLB_OK : cuda_fail(e, "init_host order");
 }
 
 ddflb_status ddflb_step(ddflb_ctx* c, int64_t n) {
@@ -379,26 +402,60 @@ ddflb_status ddflb_derived(ddflb_ctx* c, float* dxux, float* dyux, float* dxuy, 
   return check_launch(launch_fields(c->L, fptr(c, c->cur), gptr(c, c->cur), fp), "derived");
 }
 
-ddflb_status ddflb_fields_host(ddflb_ctx* c, float* rho, float* ux, float* uy, float* phi,
-                               float* sxx, float* sxy, float* syy, float* omega) {
+ddflb_status ddflb_fields_host_async(ddflb_ctx* c, float* rho, float* ux, float* uy, float* phi,
+                                     float* sxx, float* sxy, float* syy, float* omega) {
   if (!c) return fail(DDFLB_EINVAL, "NULL handle");
-  if (!c->stage) return fail(DDFLB_EINVAL, "context created without DDFLB_FLAG_HOST_IO");
+  if (!c->stage_out) return fail(DDFLB_EINVAL, "context created without DDFLB_FLAG_HOST_IO");
   const size_t n = (size_t)c->p.nx * c->p.ny;
   float* host[8] = {rho, ux, uy, phi, sxx, sxy, syy, omega};
   FieldPtrs fp{};
-  for (int k = 0; k < 8; ++k) fp.p[k] = host[k] ? c->stage + k * n : nullptr;
+  for (int k = 0; k < 8; ++k) fp.p[k] = host[k] ? c->stage_out + k * n : nullptr;
+  cudaStream_t cs = c->io ? c->io : c->L.stream;
+  // the fields kernel waits until the previous download has drained the staging area
+  cudaError_t e = c->io ? cudaStreamWaitEvent(c->L.stream, c->ev_out_free, 0) : cudaSuccess;
+  if (e != cudaSuccess) return cuda_fail(e, "fields_host order");
   at_time(c, c->step);
   ddflb_status s =
       check_launch(launch_fields(c->L, fptr(c, c->cur), gptr(c, c->cur), fp), "fields_host");
   if (s != DDFLB_OK) return s;
+  e = io_order(c, cs, c->ev_out_ready, c->L.stream);
+  if (e != cudaSuccess) return cuda_fail(e, "fields_host order");
   for (int k = 0; k < 8; ++k) {
     if (!host[k]) continue;
-    cudaError_t e = cudaMemcpyAsync(host[k], fp.p[k], n * sizeof(float), cudaMemcpyDeviceToHost,
-                                    c->L.stream);
+    e = cudaMemcpyAsync(host[k], fp.p[k], n * sizeof(float), cudaMemcpyDeviceToHost, cs);
     if (e != cudaSuccess) return cuda_fail(e, "fields_host copy");
   }
-  cudaError_t e = cudaStreamSynchronize(c->L.stream);
-  return e == cudaSuccess ? DDFLB_OK : cuda_fail(e, "fields_host sync");
+  e = c->io ? cudaEventRecord(c->ev_out_free, cs) : cudaSuccess;
+  return e == cudaSuccess ? DDFLB_OK : cuda_fail(e, "fields_host order");
+}
+
+ddflb_status ddflb_fields_host(ddflb_ctx* c, float* rho, float* ux, float* uy, float* phi,
+                               float* sxx, float* sxy, float* syy, float* omega) {
+  ddflb_status s = ddflb_fields_host_async(c, rho, ux, uy, phi, sxx, sxy, syy, omega);
+  return s == DDFLB_OK ? ddflb_io_wait(c) : s;
+}
+
+ddflb_status ddflb_io_wait(ddflb_ctx* c) {
+  if (!c) return fail(DDFLB_EINVAL, "NULL handle");
+  cudaError_t e = cudaStreamSynchronize(c->io ? c->io : c->L.stream);
+  return e == cudaSuccess ? DDFLB_OK : cuda_fail(e, "io_wait");
+}
+
+ddflb_status ddflb_set_io_stream(ddflb_ctx* c, void* io_stream) {
+  if (!c) return fail(DDFLB_EINVAL, "NULL handle");
+  if (!c->stage) return fail(DDFLB_EINVAL, "context created without DDFLB_FLAG_HOST_IO");
+  if (io_stream && !c->ev_in_free) {
+    cudaEvent_t* evs[4] = {&c->ev_in_free, &c->ev_in_ready, &c->ev_out_ready, &c->ev_out_free};
+    for (cudaEvent_t* ev : evs) {
+      cudaError_t e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+      if (e != cudaSuccess) return cuda_fail(e, "io events");
+    }
+  }
+  // copies queued so far complete before the streams change roles
+  cudaError_t e = cudaStreamSynchronize(c->io ? c->io : c->L.stream);
+  if (e != cudaSuccess) return cuda_fail(e, "set_io_stream");
+  c->io = (cudaStream_t)io_stream;
+  return DDFLB_OK;
 }
 
 ddflb_status ddflb_populations(ddflb_ctx* c, float* f, float* g) {
@@ -451,6 +508,11 @@ ddflb_status ddflb_set_state(ddflb_ctx* c, const void* src, size_t bytes, int64_
 }
 
 ddflb_status ddflb_destroy(ddflb_ctx* c) {
+  if (c && c->ev_in_free) {
+    cudaEvent_t evs[4] = {c->ev_in_free, c->ev_in_ready, c->ev_out_ready, c->ev_out_free};
+    for (cudaEvent_t ev : evs)
+      if (ev) cudaEventDestroy(ev);
+  }
   delete c;
   return DDFLB_OK;
 }

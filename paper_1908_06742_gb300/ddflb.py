@@ -66,6 +66,9 @@ SIGNATURES = {
     "ddflb_fields": (ctypes.c_int, [_VP] + [_FP] * 8),
     "ddflb_fields_host": (ctypes.c_int, [_VP] + [_FP] * 8),
     "ddflb_derived": (ctypes.c_int, [_VP] + [_FP] * 10),
+    "ddflb_fields_host_async": (ctypes.c_int, [_VP] + [_FP] * 8),
+    "ddflb_set_io_stream": (ctypes.c_int, [_VP, _VP]),
+    "ddflb_io_wait": (ctypes.c_int, [_VP]),
     "ddflb_populations": (ctypes.c_int, [_VP, _FP, _FP]),
     "ddflb_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double),
@@ -307,6 +310,22 @@ class Lattice:
         _check(self.lib.ddflb_fields_host(
             self._h, *[(out[k].data_ptr() if k in out else None) for k in FIELD_NAMES]))
         return out
+
+    def fields_host_async(self, out: dict) -> dict:
+        """Queue the fields into host float32 tensors (pinned); valid after io_wait()."""
+        _check(self.lib.ddflb_fields_host_async(
+            self._h, *[(out[k].data_ptr() if k in out else None) for k in FIELD_NAMES]))
+        return out
+
+    def set_io_stream(self, stream):
+        """Run host copies on ``stream`` (a torch.cuda.Stream; None: the context stream)."""
+        self._io = stream
+        _check(self.lib.ddflb_set_io_stream(self._h, None if stream is None else stream.cuda_stream))
+        return self
+
+    def io_wait(self):
+        _check(self.lib.ddflb_io_wait(self._h))
+        return self
 
     def populations(self):
         f, g = self._empty(9), self._empty(9)
