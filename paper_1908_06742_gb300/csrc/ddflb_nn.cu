@@ -10,6 +10,7 @@
 // GEMM convention: C[M][N] = A[M][K] . B[N][K]^T (both operands K-contiguous,
 // row-major), i.e. a convolution forward pass is C = im2col(X) . W^T with
 // W[Cout][3][3][Cin].
+#include <cuda.h>  // CUtensorMap and its enums (types only; the encoder is looked up at run time)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -157,6 +158,297 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs g) {
           if (g.Cb) g.Cb[(size_t)r * g.ldcb + c + e] = __float2bfloat16_rn(v);
         }
       }
+}
+
+// ------------------------------------------------------------------ tcgen05 GEMM
+// The same contraction on the 5th-generation tensor cores, warp-specialised,
+// one CTA (4 warps) per 128 x BN tile of C (BN = 32, 64 or 128 from N):
+//  - producer (warp 0, one thread): TMA (cp.async.bulk.tensor, 2-D tensor maps
+//    over A [M][K] and B [N][K]) fills a ring of STAGES shared-memory slots,
+//    one box of 64 K-elements (128 B) x rows per operand, written with the
+//    128-byte swizzle: the canonical K-major SWIZZLE_128B layout, 8-row x 128-B
+//    atoms of 1024 B stacked along M/N (stride byte offset 1024), the 16-byte
+//    chunks of row r permuted by r mod 8; the K = 16 slices of a 64-wide step
+//    start 32 B apart inside the atom.  The slot's `full` mbarrier counts the
+//    bytes in (expect_tx); before refilling a slot the producer waits on its
+//    `empty` mbarrier;
+//  - MMA issuer (warp 1, one thread): waits on `full`, issues tcgen05.mma
+//    (kind::f16, BF16 x BF16 -> FP32, M = 128, N = BN, K = 16 each) into an
+//    accumulator in tensor memory (128 lanes x BN columns), tcgen05.commit
+//    arrives on `empty` once those MMAs have read the slot, and on `done` after
+//    the last;
+//  - epilogue (all 4 warps): wait on `done`, read lanes 32w..32w+31 (rows of
+//    C) with tcgen05.ld, add the bias, apply the activation, store.
+// TMA zero-fills rows and K past the tensor edges.  Every mbarrier wait is
+// bounded (globaltimer, 1 s): on expiry the CTA records an error
+// (ddflb_nn_take_error), skips the epilogue, waits (bounded) for its copies in
+// flight, frees its tensor memory and returns.
+namespace tc {
+constexpr int BM = 128, BK = 64;
+constexpr int THREADS = 128;
+template <int BN>
+struct Cfg {
+  static constexpr int STAGES = BN == 128 ? 4 : 6;
+  static constexpr int A_TILE = BM * BK * 2, B_TILE = BN * BK * 2;  // bytes per slot
+  static constexpr int STAGE = A_TILE + B_TILE;
+  static constexpr int SMEM = STAGES * STAGE + 1024 + 256;  // + alignment, barriers, slot
+  static constexpr uint32_t COLS = BN < 32 ? 32 : BN;       // tensor-memory columns
+  static constexpr uint32_t SBO = 1024;  // 8 rows x 128 B
+  // instruction descriptor: D FP32 (bits 4-5 = 1), A and B BF16 (bits 7-9, 10-12 = 1),
+  // both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
+  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
+                                    ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+};
+}  // namespace tc
+
+__device__ int g_tc_error;  // set (1) when a bounded wait of the tcgen05 GEMM ran out
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// shared-memory matrix descriptor for a K-major SWIZZLE_128B operand: start
+// address >> 4 (bits 0-13), leading byte offset 16 B (unused for this layout,
+// bits 16-29), stride byte offset >> 4 (bits 32-45), descriptor version 1
+// (bits 46-47), layout type 2 = 128-byte swizzle (bits 61-63)
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// bounded wait for the completion of the mbarrier phase with the given parity
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const uint64_t deadline = globaltimer_ns() + 1000000000ull;
+  for (uint32_t it = 0; it < (1u << 24); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 255) == 255 && globaltimer_ns() > deadline) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// one 2-D TMA box (x = K element, y = row) into shared memory, counted on `bar`
+__device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                       uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+#define DDFLB_R8(i) "=r"(r[i]), "=r"(r[i + 1]), "=r"(r[i + 2]), "=r"(r[i + 3]), \
+                    "=r"(r[i + 4]), "=r"(r[i + 5]), "=r"(r[i + 6]), "=r"(r[i + 7])
+
+// 32 consecutive FP32 columns of the calling thread's tensor-memory lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t r[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : DDFLB_R8(0), DDFLB_R8(8), DDFLB_R8(16), DDFLB_R8(24)
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+#undef DDFLB_R8
+
+template <int BN>
+__global__ void __launch_bounds__(tc::THREADS) k_gemm_tc(const __grid_constant__ CUtensorMap tmA,
+                                                         const __grid_constant__ CUtensorMap tmB,
+                                                         GemmArgs g) {
+  using C = tc::Cfg<BN>;
+  constexpr int S = C::STAGES;
+  extern __shared__ uint8_t dsmem[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // 1024-byte aligned ring of slots, then the mbarriers full[S], empty[S], done
+  // and the tensor-memory address slot
+  const uint32_t raw = smem_u32(dsmem);
+  const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(dsmem + pad + S * C::STAGE);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * S + 1);
+  const uint32_t tiles_u = raw + pad;
+  const uint32_t full_u = smem_u32(bars), empty_u = full_u + 8 * S, done_u = full_u + 16 * S;
+
+  if (tid == 0) {
+    for (int i = 0; i < S; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full_u + 8 * i) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(empty_u + 8 * i) : "memory");
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(done_u) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tslot)),
+                 "r"(C::COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  const int m0 = blockIdx.y * tc::BM, n0 = blockIdx.x * BN;
+  const int kbeg = blockIdx.z * g.kchunk, kend = min(g.K, kbeg + g.kchunk);
+  const int nk = kend > kbeg ? (kend - kbeg + tc::BK - 1) / tc::BK : 0;
+  int bad = 0;  // this thread's bounded wait ran out
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- producer
+    int kt = 0;
+    for (; kt < nk; ++kt) {
+      const int st = kt % S;
+      // slot st was last read by the MMAs of step kt - S
+      if (kt >= S && !mbar_wait(empty_u + 8 * st, ((kt / S) - 1) & 1)) {
+        bad = 1;
+        break;
+      }
+      const uint32_t bar = full_u + 8 * st;
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                   "r"(C::STAGE)
+                   : "memory");
+      const uint32_t sa = tiles_u + st * C::STAGE, sb = sa + C::A_TILE;
+      const int k0 = kbeg + kt * tc::BK;  // a multiple of 64 elements (128 B)
+      tma_2d(sa, &tmA, k0, m0, bar);
+      tma_2d(sb, &tmB, k0, n0, bar);
+    }
+    if (bad) {
+      // let the copies already requested land before the CTA's memory goes away
+      for (int k2 = kt - 1; k2 >= 0 && k2 >= kt - S; --k2)
+        mbar_wait(full_u + 8 * (k2 % S), (k2 / S) & 1);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    for (int kt = 0; kt < nk; ++kt) {
+      const int st = kt % S;
+      if (!mbar_wait(full_u + 8 * st, (kt / S) & 1)) {
+        bad = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t a0 = tiles_u + st * C::STAGE, b0 = a0 + C::A_TILE;
+#pragma unroll
+      for (int kk = 0; kk < tc::BK / 16; ++kk) {
+        // K = 16 elements = 32 B further along the swizzled 128-B rows
+        const uint64_t ad = smem_desc_sw128(a0 + kk * 32, C::SBO);
+        const uint64_t bd = smem_desc_sw128(b0 + kk * 32, C::SBO);
+        const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(C::IDESC), "r"(acc)
+            : "memory");
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              empty_u + 8 * st)
+          : "memory");
+    }
+    // `done` fires once every MMA issued above has completed
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            done_u)
+        : "memory");
+  }
+  __syncwarp();
+  // every warp waits for the accumulator (lane 0 polls, the warp follows)
+  if (lane == 0 && !bad && !mbar_wait(done_u, 0)) bad = 1;
+  const int aborted = __syncthreads_or(bad);
+  tc_fence_after();
+  if (aborted) {
+    if (tid == 0) atomicExch(&g_tc_error, 1);
+  } else {
+    const int r = m0 + warp * 32 + lane;
+    const bool vf = g.Cf && !g.partial && (g.ldc & 3) == 0 && ((uintptr_t)g.Cf & 15) == 0;
+    const bool vb = g.Cb && !g.partial && (g.ldcb & 7) == 0 && ((uintptr_t)g.Cb & 15) == 0;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+      uint32_t v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      if (r >= g.M) continue;
+      const int cb = n0 + c0;
+      float x[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        float t = nk > 0 ? __uint_as_float(v[i]) : 0.0f;
+        if (!g.partial) {
+          if (g.bias && cb + i < g.N) t += g.bias[cb + i];
+          t = act_fwd(t, g.act);
+        }
+        x[i] = t;
+      }
+      if (g.partial) {
+        float* p = g.partial + ((size_t)blockIdx.z * g.M + r) * g.N;
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+          if (cb + i < g.N) p[cb + i] = x[i];
+        continue;
+      }
+      const bool full_chunk = cb + 32 <= g.N;
+      if (g.Cf) {
+        float* p = g.Cf + (size_t)r * g.ldc + cb;
+        if (vf && full_chunk) {
+#pragma unroll
+          for (int i = 0; i < 32; i += 4) {
+            float4 o = make_float4(x[i], x[i + 1], x[i + 2], x[i + 3]);
+            if (g.accumulate) {
+              const float4 q = *reinterpret_cast<const float4*>(p + i);
+              o.x += q.x; o.y += q.y; o.z += q.z; o.w += q.w;
+            }
+            *reinterpret_cast<float4*>(p + i) = o;
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+            if (cb + i < g.N) p[i] = g.accumulate ? p[i] + x[i] : x[i];
+        }
+      }
+      if (g.Cb) {
+        bf16* p = g.Cb + (size_t)r * g.ldcb + cb;
+        if (vb && full_chunk) {
+#pragma unroll
+          for (int i = 0; i < 32; i += 8) {
+            __align__(16) bf16 h[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) h[e] = __float2bfloat16_rn(x[i + e]);
+            *reinterpret_cast<uint4*>(p + i) = *reinterpret_cast<const uint4*>(h);
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+            if (cb + i < g.N) p[i] = __float2bfloat16_rn(x[i]);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(C::COLS)
+                 : "memory");
+  }
 }
 
 // split-K: C = sum over slices z (fixed order) of partial[z]; then bias, act
@@ -422,7 +714,104 @@ ddflb_status bad(const char* msg) {
 }
 }  // namespace
 
+namespace {
+int g_gemm_path = 0;  // 0: tcgen05 kernel (default), 1: mma.sync kernel
+
+// cuTensorMapEncodeTiled from the driver, looked up through the runtime (no
+// link-time dependency on the driver library)
+typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_fn() {
+  static EncodeTiled fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiled)p;
+  }
+  return fn;
+}
+
+// 2-D map over a row-major BF16 matrix [rows][K] (row stride ld elements):
+// boxes of 64 K-elements (128 B) x box_rows rows, 128-byte swizzle, zero fill
+// outside
+bool make_map(CUtensorMap* m, const void* base, int rows, int K, int ld, int box_rows) {
+  EncodeTiled fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN>
+ddflb_status gemm_tc_bn(const GemmArgs& g, dim3 grid, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_gemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             tc::Cfg<BN>::SMEM) != cudaSuccess)
+      return launched("gemm tcgen05 attribute");
+    attr = true;
+  }
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, g.A, g.M, g.K, g.lda, tc::BM) || !make_map(&mb, g.B, g.N, g.K, g.ldb, BN))
+    return bad("gemm: TMA tensor map encoding failed");
+  k_gemm_tc<BN><<<grid, tc::THREADS, tc::Cfg<BN>::SMEM, s>>>(ma, mb, g);
+  return launched("gemm tcgen05");
+}
+
+// N tile: the smallest of 32, 64, 128 that covers N (wider N: 128-column tiles)
+ddflb_status gemm_tc(GemmArgs g, int splits, cudaStream_t s) {
+  int kchunk = g.K;
+  if (splits > 1) {
+    kchunk = (g.K + splits - 1) / splits;
+    kchunk = (kchunk + tc::BK - 1) / tc::BK * tc::BK;
+  }
+  const int z = (g.K + kchunk - 1) / kchunk;
+  g.kchunk = kchunk;
+  const int bn = g.N <= 32 ? 32 : g.N <= 64 ? 64 : 128;
+  dim3 grid((g.N + bn - 1) / bn, (g.M + tc::BM - 1) / tc::BM, z);
+  ddflb_status st = bn == 32   ? gemm_tc_bn<32>(g, grid, s)
+                    : bn == 64 ? gemm_tc_bn<64>(g, grid, s)
+                               : gemm_tc_bn<128>(g, grid, s);
+  if (st != DDFLB_OK || splits == 1) return st;
+  k_splitk_reduce<<<grid_for((int64_t)g.M * g.N), 256, 0, s>>>(g.partial, z, g.M, g.N, g.Cf, g.ldc,
+                                                               g.bias, g.act, g.accumulate);
+  return launched("gemm tcgen05 split-K");
+}
+}  // namespace
+
 extern "C" {
+
+ddflb_status ddflb_nn_set_gemm_path(int32_t path) {
+  if (path < 0 || path > 1) return bad("gemm path must be 0 (tcgen05) or 1 (mma.sync)");
+  g_gemm_path = path;
+  return DDFLB_OK;
+}
+
+ddflb_status ddflb_nn_take_error(int32_t* error, void* stream) {
+  if (!error) return bad("take_error: NULL output");
+  int* dev = nullptr;
+  cudaError_t e = cudaGetSymbolAddress((void**)&dev, g_tc_error);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(error, dev, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dev, 0, sizeof(int), (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    ddflb::set_error(cudaGetErrorString(e));
+    return DDFLB_ECUDA;
+  }
+  return DDFLB_OK;
+}
 
 ddflb_status ddflb_nn_gemm(const void* A, const void* B, int32_t M, int32_t N, int32_t K,
                            int32_t lda, int32_t ldb, float* Cf, int32_t ldc, void* Cb,
@@ -435,6 +824,15 @@ ddflb_status ddflb_nn_gemm(const void* A, const void* B, int32_t M, int32_t N, i
   if (act < 0 || act > 1) return bad("gemm: act must be 0 (none) or 1 (leaky ReLU)");
   if (splits < 1) return bad("gemm: splits < 1");
   cudaStream_t s = (cudaStream_t)stream;
+  if (splits > 1 && (!Cf || Cb || !partial))
+    return bad("gemm: split-K needs Cf and partial (and no Cb)");
+  if (g_gemm_path == 0) {
+    GemmArgs g{(const bf16*)A, (const bf16*)B, M, N, K, lda, ldb, splits > 1 ? nullptr : Cf,
+               splits > 1 ? nullptr : (bf16*)Cb, ldc, ldcb, bias, act, accumulate, K,
+               splits > 1 ? partial : nullptr};
+    if (splits > 1) g.Cf = Cf;  // read by the split-K reduction only
+    return gemm_tc(g, splits, s);
+  }
   if (splits == 1) {
     GemmArgs g{(const bf16*)A, (const bf16*)B, M, N, K, lda, ldb, Cf, (bf16*)Cb, ldc, ldcb,
                bias, act, accumulate, K, nullptr};

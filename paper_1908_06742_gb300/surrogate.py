@@ -26,6 +26,7 @@ from . import ddflb as D
 
 CIN, COUT = 16, 8            # padded input / output channels (5 and 5 used)
 LEAKY = 1
+GEMM_PATH = 0       # GEMM kernel the library uses by default (0 tcgen05, 1 mma.sync)
 
 
 def specs(c: int, cin: int = CIN, cout: int = COUT):

@@ -3,6 +3,7 @@ against a float64 matrix product of the same BF16 inputs, and the full U-Net
 (output and every parameter gradient) against the FP64 network oracle run on
 the GPU's BF16 weights and input.  BF16 rounding of the activations between
 layers bounds the agreement (about 2^-9 per layer)."""
+import ctypes
 import math
 
 import numpy as np
@@ -29,10 +30,29 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
+@pytest.fixture
+def gemm_path():
+    """Select a GEMM kernel for one test, then restore the default."""
+    lib = D.load()
+    yield lambda p: D._check(lib.ddflb_nn_set_gemm_path(p))
+    D._check(lib.ddflb_nn_set_gemm_path(S.GEMM_PATH))
+
+
+def take_error():
+    e = ctypes.c_int32(-1)
+    D._check(D.load().ddflb_nn_take_error(ctypes.byref(e), None))
+    return e.value
+
+
+@pytest.mark.parametrize("path", [0, 1])
 @pytest.mark.parametrize("M,N,K,splits,bias,act", [
     (1, 1, 8, 1, False, 0), (130, 70, 40, 1, True, 1), (257, 129, 136, 1, True, 0),
-    (1000, 64, 4096, 7, False, 0), (64, 2304, 8192, 16, True, 1), (300, 8, 32, 1, True, 0)])
-def test_gemm_against_float64(M, N, K, splits, bias, act):
+    (1000, 64, 4096, 7, False, 0), (64, 2304, 8192, 16, True, 1), (300, 8, 32, 1, True, 0),
+    (4096, 128, 576, 1, True, 1), (513, 256, 1152, 3, False, 0)])
+def test_gemm_against_float64(M, N, K, splits, bias, act, path, gemm_path):
+    """Both GEMM kernels (0: tcgen05, 1: mma.sync) against a float64 product of
+    the same BF16 operands, over ragged multi-tile shapes and split-K."""
+    gemm_path(path)
     g = torch.Generator().manual_seed(M * 7 + N)
     A = torch.randn(M, K, generator=g).to(torch.bfloat16).cuda()
     Bm = torch.randn(N, K, generator=g).to(torch.bfloat16).cuda()
@@ -58,6 +78,28 @@ def test_gemm_against_float64(M, N, K, splits, bias, act):
         np.abs(got - ref).max()
     if Cb is not None:
         assert rel(Cb.double().cpu().numpy(), ref) < 4e-3
+    assert take_error() == 0
+
+
+@pytest.mark.parametrize("path", [0, 1])
+def test_gemm_accumulate_and_strides(path, gemm_path):
+    """accumulate = 1 adds to Cf; lda, ldb, ldc larger than K and N."""
+    gemm_path(path)
+    M, N, K, lda, ldb, ldc = 333, 96, 200, 216, 208, 100
+    g = torch.Generator().manual_seed(5)
+    A = torch.randn(M, lda, generator=g).to(torch.bfloat16).cuda()
+    Bm = torch.randn(N, ldb, generator=g).to(torch.bfloat16).cuda()
+    C0 = torch.randn(M, ldc, generator=g).cuda()
+    Cf = C0.clone()
+    D._check(D.load().ddflb_nn_gemm(A.data_ptr(), Bm.data_ptr(), M, N, K, lda, ldb, Cf.data_ptr(),
+                                    ldc, None, 0, None, 0, 1, 1, None,
+                                    torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    ref = C0.double().cpu().numpy()
+    ref[:, :N] += A[:, :K].double().cpu().numpy() @ Bm[:, :K].double().cpu().numpy().T
+    got = Cf.double().cpu().numpy()
+    assert np.abs(got - ref).max() < 1e-4
+    assert take_error() == 0
 
 
 def test_gemm_rejects_bad_shapes():
