@@ -410,7 +410,9 @@ ddflb_status ddflb_nn_upsample_bwd(const float* dY, int32_t B, int32_t H, int32_
 /* g *= act'(.) read from the activation output y (BF16); optional BF16 copy gb. */
 ddflb_status ddflb_nn_act_bwd(float* g, const void* y, int64_t rows, int32_t C, int32_t csg,
                               int32_t csy, int32_t act, void* gb, int32_t csb, void* stream);
-/* db[c] = sum over rows of g[r][c] (FP32). */
+/* db[c] = sum over rows of g[r][c] (FP32), in a fixed order.  For 4096 rows or
+ * more (and C <= 4096) the partial sums go through one scratch array of the
+ * library, so such calls on different streams must not overlap. */
 ddflb_status ddflb_nn_bias_grad(const float* g, int64_t rows, int32_t C, int32_t cs, float* db,
                                 void* stream);
 /* Mean squared error of n FP32 values into *dev_loss (FP64), optional gradient

@@ -504,6 +504,78 @@ __global__ void k_im2col_t(const bf16* __restrict__ X, int B, int H, int W, int 
   }
 }
 
+// Vector forms (16-byte chunks of 8 channels; used when C, cs are multiples of
+// 8 and the buffers 16-byte aligned): one thread per (pixel, tap, chunk).
+__global__ void k_im2col_v8(const bf16* __restrict__ X, int B, int H, int W, int C8, int cs,
+                            bf16* __restrict__ col) {
+  const int64_t total = (int64_t)B * H * W * 9 * C8;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int c8 = (int)(i % C8);
+    const int64_t r = i / C8;
+    const int tap = (int)(r % 9);
+    const int64_t p = r / 9;
+    const int w = (int)(p % W);
+    const int64_t t = p / W;
+    const int h = (int)(t % H), b = (int)(t / H);
+    const int hh = h + tap / 3 - 1, ww = w + tap % 3 - 1;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (hh >= 0 && hh < H && ww >= 0 && ww < W)
+      v = *reinterpret_cast<const uint4*>(X + (((int64_t)b * H + hh) * W + ww) * cs + c8 * 8);
+    *reinterpret_cast<uint4*>(col + i * 8) = v;
+  }
+}
+
+// transposed: thread (row group k8 = tap*C8 + c8, pixel p), pixels fastest, so
+// each of the 8 rows it writes is written coalesced across the warp
+__global__ void k_im2col_t_v8(const bf16* __restrict__ X, int B, int H, int W, int C8, int cs,
+                              bf16* __restrict__ colT) {
+  const int64_t P = (int64_t)B * H * W, total = P * 9 * C8;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = i % P;
+    const int k8 = (int)(i / P);
+    const int c8 = k8 % C8, tap = k8 / C8;
+    const int w = (int)(p % W);
+    const int64_t t = p / W;
+    const int h = (int)(t % H), b = (int)(t / H);
+    const int hh = h + tap / 3 - 1, ww = w + tap % 3 - 1;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (hh >= 0 && hh < H && ww >= 0 && ww < W)
+      v = *reinterpret_cast<const uint4*>(X + (((int64_t)b * H + hh) * W + ww) * cs + c8 * 8);
+    const bf16* e = reinterpret_cast<const bf16*>(&v);
+    bf16* dst = colT + ((int64_t)tap * C8 * 8 + c8 * 8) * P + p;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) dst[j * P] = e[j];
+  }
+}
+
+// col2im with 4 channels per thread (C, cs multiples of 4, 16-byte aligned)
+__global__ void k_col2im_v4(const float* __restrict__ dcol, int B, int H, int W, int C4,
+                            float* __restrict__ dX, int cs) {
+  const int64_t total = (int64_t)B * H * W * C4;
+  const int C = C4 * 4;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int c4 = (int)(i % C4);
+    const int64_t p = i / C4;
+    const int w = (int)(p % W);
+    const int64_t t = p / W;
+    const int h = (int)(t % H), b = (int)(t / H);
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int ho = h - (tap / 3 - 1), wo = w - (tap % 3 - 1);  // output pixel reading (h, w)
+      if (ho >= 0 && ho < H && wo >= 0 && wo < W) {
+        const float4 q = *reinterpret_cast<const float4*>(
+            dcol + ((((int64_t)b * H + ho) * W + wo) * 9 + tap) * C + c4 * 4);
+        s.x += q.x; s.y += q.y; s.z += q.z; s.w += q.w;
+      }
+    }
+    *reinterpret_cast<float4*>(dX + p * cs + c4 * 4) = s;
+  }
+}
+
 // col2im: dX[b][h][w][c] = sum over taps of dcol[pixel that reads (h, w)][tap][c]
 __global__ void k_col2im(const float* __restrict__ dcol, int B, int H, int W, int C,
                          float* __restrict__ dX, int cs) {
@@ -618,6 +690,41 @@ __global__ void k_act_bwd(float* __restrict__ g, const bf16* __restrict__ y, int
 }
 
 // db[c] = sum over rows of g[r][c] (fixed order per channel)
+// Two-pass column sums for wide row counts: pass 1, block (channel group of 32,
+// row chunk) with 8 warps striding the chunk's rows (coalesced 128-byte row
+// segments), partial sums to a fixed scratch; pass 2 adds the chunks in order
+// (deterministic).
+constexpr int kBiasChunks = 64, kBiasMaxC = 4096;
+__device__ float g_bias_partial[kBiasChunks * kBiasMaxC];
+
+__global__ void __launch_bounds__(256) k_bias_grad_part(const float* __restrict__ g,
+                                                        int64_t rows, int C, int cs) {
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + lane;
+  const int64_t per = (rows + gridDim.y - 1) / gridDim.y;
+  const int64_t r0 = blockIdx.y * per, r1 = r0 + per < rows ? r0 + per : rows;
+  float s = 0.f;
+  if (c < C)
+    for (int64_t r = r0 + wp; r < r1; r += 8) s += g[r * cs + c];
+  __shared__ float sh[8][32];
+  sh[wp][lane] = s;
+  __syncthreads();
+  if (wp == 0 && c < C) {
+    float t = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += sh[k][lane];
+    g_bias_partial[(int64_t)blockIdx.y * C + c] = t;
+  }
+}
+
+__global__ void k_bias_grad_final(int C, int chunks, float* __restrict__ db) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  float t = 0.f;
+  for (int k = 0; k < chunks; ++k) t += g_bias_partial[(int64_t)k * C + c];
+  db[c] = t;
+}
+
 __global__ void k_bias_grad(const float* __restrict__ g, int64_t rows, int C, int cs,
                             float* __restrict__ db) {
   const int c = blockIdx.x;
@@ -857,12 +964,20 @@ ddflb_status ddflb_nn_im2col(const void* X, int32_t B, int32_t H, int32_t W, int
                              int32_t cs, void* col, int32_t transposed, void* stream) {
   if (!X || !col || B <= 0 || H <= 0 || W <= 0 || C <= 0 || cs < C) return bad("im2col: bad args");
   const int64_t n = (int64_t)B * H * W * 9 * C;
-  if (transposed)
-    k_im2col_t<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>((const bf16*)X, B, H, W, C, cs,
-                                                              (bf16*)col);
-  else
-    k_im2col<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>((const bf16*)X, B, H, W, C, cs,
-                                                            (bf16*)col);
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool v8 = C % 8 == 0 && cs % 8 == 0 && (uintptr_t)X % 16 == 0 && (uintptr_t)col % 16 == 0;
+  if (v8) {
+    if (transposed)
+      k_im2col_t_v8<<<grid_for(n / 8), 256, 0, st>>>((const bf16*)X, B, H, W, C / 8, cs,
+                                                     (bf16*)col);
+    else if (!transposed)
+      k_im2col_v8<<<grid_for(n / 8), 256, 0, st>>>((const bf16*)X, B, H, W, C / 8, cs,
+                                                   (bf16*)col);
+  } else if (transposed) {
+    k_im2col_t<<<grid_for(n), 256, 0, st>>>((const bf16*)X, B, H, W, C, cs, (bf16*)col);
+  } else {
+    k_im2col<<<grid_for(n), 256, 0, st>>>((const bf16*)X, B, H, W, C, cs, (bf16*)col);
+  }
   return launched("im2col");
 }
 
@@ -870,7 +985,10 @@ ddflb_status ddflb_nn_col2im(const float* dcol, int32_t B, int32_t H, int32_t W,
                              float* dX, int32_t cs, void* stream) {
   if (!dcol || !dX || B <= 0 || H <= 0 || W <= 0 || C <= 0 || cs < C) return bad("col2im: bad args");
   const int64_t n = (int64_t)B * H * W * C;
-  k_col2im<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(dcol, B, H, W, C, dX, cs);
+  if (C % 4 == 0 && cs % 4 == 0 && (uintptr_t)dcol % 16 == 0 && (uintptr_t)dX % 16 == 0)
+    k_col2im_v4<<<grid_for(n / 4), 256, 0, (cudaStream_t)stream>>>(dcol, B, H, W, C / 4, dX, cs);
+  else
+    k_col2im<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(dcol, B, H, W, C, dX, cs);
   return launched("col2im");
 }
 
@@ -929,7 +1047,15 @@ ddflb_status ddflb_nn_act_bwd(float* g, const void* y, int64_t rows, int32_t C, 
 ddflb_status ddflb_nn_bias_grad(const float* g, int64_t rows, int32_t C, int32_t cs, float* db,
                                 void* stream) {
   if (!g || !db || rows <= 0 || C <= 0) return bad("bias_grad: bad args");
-  k_bias_grad<<<C, 256, 0, (cudaStream_t)stream>>>(g, rows, C, cs, db);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (C <= kBiasMaxC && rows >= 4096) {
+    // the scratch is one per process: calls on different streams must not overlap
+    dim3 grid((C + 31) / 32, kBiasChunks);
+    k_bias_grad_part<<<grid, 256, 0, st>>>(g, rows, C, cs);
+    k_bias_grad_final<<<(C + 127) / 128, 128, 0, st>>>(C, kBiasChunks, db);
+  } else {
+    k_bias_grad<<<C, 256, 0, st>>>(g, rows, C, cs, db);
+  }
   return launched("bias_grad");
 }
 

@@ -168,3 +168,55 @@ def test_training_reduces_loss():
         first = first if first is not None else loss
         net.adam(lr=3e-3)
     assert loss < 0.1 * first, (first, loss)
+
+
+def im2col_np(X, C):
+    """col[p][(kh*3 + kw)*C + c] = X[b][h+kh-1][w+kw-1][c], zero padding."""
+    B, H, W, _ = X.shape
+    Xp = np.zeros((B, H + 2, W + 2, C), X.dtype)
+    Xp[:, 1:-1, 1:-1] = X[..., :C]
+    cols = [Xp[:, kh:kh + H, kw:kw + W] for kh in range(3) for kw in range(3)]
+    return np.concatenate(cols, axis=-1).reshape(B * H * W, 9 * C)
+
+
+@pytest.mark.parametrize("C,cs", [(16, 16), (32, 48), (6, 10)])
+def test_im2col_both_layouts(C, cs):
+    """Vector (C, cs multiples of 8) and scalar paths, plain and transposed."""
+    B, H, W = 3, 17, 23
+    g = torch.Generator().manual_seed(C + cs)
+    X = torch.randn(B, H, W, cs, generator=g).to(torch.bfloat16).cuda()
+    want = im2col_np(X.float().cpu().numpy(), C)
+    lib = D.load()
+    for transposed in (0, 1):
+        out = torch.empty(want.size, dtype=torch.bfloat16, device="cuda")
+        D._check(lib.ddflb_nn_im2col(X.data_ptr(), B, H, W, C, cs, out.data_ptr(), transposed, None))
+        torch.cuda.synchronize()
+        got = out.float().cpu().numpy().reshape(want.T.shape if transposed else want.shape)
+        np.testing.assert_array_equal(got, want.T if transposed else want)
+
+
+@pytest.mark.parametrize("C,cs", [(32, 32), (8, 12), (5, 5)])
+def test_col2im_adjoint_of_im2col(C, cs):
+    """col2im sums the taps back: <im2col(x), d> = <x, col2im(d)> (adjoint)."""
+    B, H, W = 2, 19, 21
+    g = torch.Generator().manual_seed(C)
+    dcol = torch.randn(B * H * W, 9 * C, generator=g).cuda()
+    dX = torch.zeros(B, H, W, cs, device="cuda")
+    D._check(D.load().ddflb_nn_col2im(dcol.data_ptr(), B, H, W, C, dX.data_ptr(), cs, None))
+    torch.cuda.synchronize()
+    x = np.random.default_rng(C).standard_normal((B, H, W, C))
+    lhs = np.sum(im2col_np(x, C) * dcol.double().cpu().numpy())
+    rhs = np.sum(x * dX.double().cpu().numpy()[..., :C])
+    assert abs(lhs - rhs) < 1e-9 * np.sum(np.abs(dcol.double().cpu().numpy())) * 10
+
+
+@pytest.mark.parametrize("rows,C,cs", [(100000, 32, 48), (5000, 130, 130), (300, 7, 9)])
+def test_bias_grad_column_sums(rows, C, cs):
+    g = torch.Generator().manual_seed(rows)
+    G = torch.randn(rows, cs, generator=g).cuda()
+    db = torch.empty(C, device="cuda")
+    D._check(D.load().ddflb_nn_bias_grad(G.data_ptr(), rows, C, cs, db.data_ptr(), None))
+    torch.cuda.synchronize()
+    want = G.double().cpu().numpy()[:, :C].sum(axis=0)
+    np.testing.assert_allclose(db.double().cpu().numpy(), want, rtol=0,
+                               atol=1e-5 * np.sqrt(rows))
