@@ -13,6 +13,7 @@ scaling) and the slowest rank's time counts.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import math
 import os
@@ -42,10 +43,13 @@ def parse():
                     help="scalar collision (Sec. 3 MRT, App. B SRT, App. C cascaded, App. D central)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="tg", choices=["tg", "batch", "cavity", "surrogate"],
+    ap.add_argument("--workload", default="tg",
+                    choices=["tg", "batch", "cavity", "surrogate", "gemm"],
                     help="tg: Taylor-Green throughput sweep point; batch: 512 uneven cavities; "
                          "cavity: 256^2 cavities run to steady state")
     ap.add_argument("--instances", type=int, default=512)
+    ap.add_argument("--gemm-shape", default=None,
+                    help="gemm workload: one M,N,K,splits shape instead of the U-Net set")
     return ap.parse_args()
 
 
@@ -559,6 +563,82 @@ def run_surrogate(args, world, rank, local):
     }))
 
 
+# U-Net convolution GEMMs (C = A . B^T): forward (pixels x Cout x 9 Cin) at the
+# 128^2 / batch-16 training size, and weight gradients (Cout x 9 Cin x pixels,
+# split-K)
+GEMM_SHAPES = [(262144, 32, 144, 1), (65536, 64, 288, 1), (16384, 128, 576, 1),
+               (4096, 128, 1152, 1), (65536, 128, 1152, 1), (16384, 256, 2304, 1),
+               (128, 1152, 65536, 16)]
+
+
+def run_gemm(args, world, rank, local):
+    """BF16 GEMM throughput of the surrogate's contraction shapes on both
+    tensor-core paths (0: tcgen05 + TMA, 1: mma.sync), CUDA events per shape."""
+    import torch
+    from paper_1908_06742_gb300 import build as B
+    from paper_1908_06742_gb300 import ddflb as D
+    B.build()
+    torch.cuda.set_device(local)
+    lib = D.load()
+    shapes = GEMM_SHAPES
+    if args.gemm_shape:
+        shapes = [tuple(int(v) for v in args.gemm_shape.split(","))]
+    rows, tot = [], {0: [0.0, 0.0], 1: [0.0, 0.0]}
+    st = torch.cuda.current_stream()
+    for M, N, K, sp in shapes:
+        g = torch.Generator(device="cuda").manual_seed(M + N + K)
+        A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+        Bm = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
+        C = torch.empty(M, N, device="cuda")
+        part = torch.empty(sp * M * N, device="cuda") if sp > 1 else None
+        row = {"M": M, "N": N, "K": K, "splits": sp}
+        for path in (0, 1):
+            D._check(lib.ddflb_nn_set_gemm_path(path))
+
+            def call():
+                D._check(lib.ddflb_nn_gemm(A.data_ptr(), Bm.data_ptr(), M, N, K, K, K,
+                                           C.data_ptr(), N, None, 0, None, 0, 0, sp,
+                                           None if part is None else part.data_ptr(),
+                                           st.cuda_stream))
+            for _ in range(args.warmup):
+                call()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(args.steps):
+                call()
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            fl = 2.0 * M * N * K
+            row[f"ms_path{path}"] = round(ms, 4)
+            row[f"tflops_path{path}"] = round(fl / ms / 1e9, 1)
+            tot[path][0] += fl
+            tot[path][1] += ms
+        rows.append(row)
+    D._check(lib.ddflb_nn_set_gemm_path(0))
+    err = ctypes.c_int32(-1)
+    D._check(lib.ddflb_nn_take_error(ctypes.byref(err), None))
+    if rank != 0:
+        return
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak, kind = float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        peak, kind = 1900.0, "fallback"
+    agg = {p: tot[p][0] / tot[p][1] / 1e9 for p in tot}
+    print(json.dumps({
+        "metric": "BF16 GEMM TFLOP/s, surrogate convolution shapes (aggregate)",
+        "value": round(agg[0], 1), "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(tot[0][1], 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": "U-Net convolution GEMMs (forward and weight-gradient shapes)",
+                   "kernel": "tcgen05 + TMA (path 0); mma.sync reference (path 1)"},
+        "roofline": {"bound": "tensor", "achieved": round(agg[0], 1), "peak": peak,
+                     "unit": "TFLOP/s", "frac": round(agg[0] / peak, 4), "peak_kind": kind},
+        "mma_sync_tflops": round(agg[1], 1), "device_error_word": err.value, "shapes": rows}))
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
@@ -570,6 +650,8 @@ def main():
         run_cavity(args, world, rank, local)
     elif args.workload == "surrogate":
         run_surrogate(args, world, rank, local)
+    elif args.workload == "gemm":
+        run_gemm(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:
