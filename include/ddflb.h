@@ -338,11 +338,13 @@ ddflb_status ddflb_batch_step(ddflb_batch* b, int64_t n);
 /* Local kinematics of instance i's current state, as ddflb_fields. */
 ddflb_status ddflb_batch_fields(ddflb_batch* b, int32_t i, float* rho, float* ux, float* uy,
                                 float* phi, float* sxx, float* sxy, float* syy, float* omega);
-/* Per-instance host arrays (any may be NULL): last residual, flags, the state
- * time at which the residual first fell below tol (-1: not yet) and the state
- * time of the current state.  Synchronises; ETIMEOUT if a barrier wait ran out. */
+/* Per-instance host arrays (any may be NULL): last residual, flags, the steps
+ * from the instance's last ddflb_batch_init to the check at which the residual
+ * first fell below tol (-1: not yet), the state time of its current state and
+ * the state time of its last init (so state_time - init_time steps have been
+ * run on it).  Synchronises; ETIMEOUT if a barrier wait ran out. */
 ddflb_status ddflb_batch_stats(ddflb_batch* b, double* residual, int32_t* flags,
-                               int64_t* steps_to_tol, int64_t* state_time);
+                               int64_t* steps_to_tol, int64_t* state_time, int64_t* init_time);
 /* Autotuner: times every supported tile shape at full and half residency
  * (trial_steps per timed launch, CUDA events) and keeps the fastest; returns
  * the choice and its time per step.  Runs on zeroed populations, so it

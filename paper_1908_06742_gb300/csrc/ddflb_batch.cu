@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(256) k_batch(BatchArgs A) {
             st.state_time = t + 1;
           } else if (A.tol > 0.0 && st.residual < A.tol) {
             st.flags = DDFLB_INST_CONVERGED;
-            st.steps_to_tol = t;
+            st.steps_to_tol = t - st.init_time;  // steps since this instance's init
             st.state_time = t + 1;
           }
         }
@@ -680,7 +680,7 @@ ddflb_status ddflb_batch_fields(ddflb_batch* b, int32_t i, float* rho, float* ux
 }
 
 ddflb_status ddflb_batch_stats(ddflb_batch* b, double* residual, int32_t* flags,
-                               int64_t* steps_to_tol, int64_t* state_time) {
+                               int64_t* steps_to_tol, int64_t* state_time, int64_t* init_time) {
   if (!b) return bfail(DDFLB_EINVAL, "NULL batch");
   std::vector<BatchStatus> h(b->n);
   cudaError_t e = cudaMemcpyAsync(h.data(), b->d_status, b->n * sizeof(BatchStatus),
@@ -692,6 +692,7 @@ ddflb_status ddflb_batch_stats(ddflb_batch* b, double* residual, int32_t* flags,
     if (flags) flags[i] = h[i].flags;
     if (steps_to_tol) steps_to_tol[i] = h[i].steps_to_tol;
     if (state_time) state_time[i] = h[i].flags ? h[i].state_time : b->step;
+    if (init_time) init_time[i] = h[i].init_time;
   }
   return check_sync_error(b);
 }

@@ -90,7 +90,7 @@ SIGNATURES = {
     "ddflb_batch_init": (ctypes.c_int, [_VP, ctypes.c_int32, _FP, _FP, _FP, _FP, _FP]),
     "ddflb_batch_step": (ctypes.c_int, [_VP, ctypes.c_int64]),
     "ddflb_batch_fields": (ctypes.c_int, [_VP, ctypes.c_int32] + [_FP] * 8),
-    "ddflb_batch_stats": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "ddflb_batch_stats": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "ddflb_batch_debug_skip_barrier": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "ddflb_batch_autotune": (ctypes.c_int, [_VP, ctypes.c_int32] +
                              [ctypes.POINTER(ctypes.c_int32)] * 3 + [ctypes.POINTER(ctypes.c_double)]),
@@ -462,9 +462,11 @@ class Batch:
         f = np.zeros(self.n, np.int32)
         s = np.zeros(self.n, np.int64)
         t = np.zeros(self.n, np.int64)
+        i0 = np.zeros(self.n, np.int64)
         st = self.lib.ddflb_batch_stats(self._h, r.ctypes.data, f.ctypes.data, s.ctypes.data,
-                                        t.ctypes.data)
-        return {"residual": r, "flags": f, "steps_to_tol": s, "state_time": t, "status": st}
+                                        t.ctypes.data, i0.ctypes.data)
+        return {"residual": r, "flags": f, "steps_to_tol": s, "state_time": t, "init_time": i0,
+                "status": st}
 
     def debug_skip_barrier(self, block):
         _check(self.lib.ddflb_batch_debug_skip_barrier(self._h, int(block)))

@@ -113,6 +113,14 @@ def test_convergence_freezes_instance():
     again = D.Lattice(slow).init(*start_fields(slow, 0)).step(t_tol + 1).fields()
     for k in D.FIELD_NAMES:
         assert same(frozen[k], again[k]), k
+    # re-initialised later (the batch is at state time 600), the instance
+    # counts its steps from that init
+    b.init(0, *start_fields(slow, 0))
+    b.step(600)
+    st2 = b.stats()
+    assert st2["init_time"][0] == 600
+    assert st2["flags"][0] == D.INST_CONVERGED and st2["steps_to_tol"][0] == t_tol
+    assert st2["state_time"][0] - st2["init_time"][0] == t_tol + 1
 
 
 def test_divergence_is_isolated():
