@@ -178,8 +178,11 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return t;  // valid in thread 0
 }
 
+// At most 64 registers a thread (4 CTAs of 256 threads or 8 of 128 per SM):
+// the step is latency-bound on memory, so resident warps matter more than the
+// few values that spill.
 template <typename S>
-__global__ void __launch_bounds__(256) k_batch(BatchArgs A) {
+__global__ void __launch_bounds__(256, 4) k_batch(BatchArgs A) {
   __shared__ BatchInst sI;
   __shared__ double sh[8];
   __shared__ int sActive;
@@ -190,6 +193,7 @@ __global__ void __launch_bounds__(256) k_batch(BatchArgs A) {
   // in shared memory once per instance change, not once per tile
   const int per = (A.ntiles + gridDim.x - 1) / gridDim.x;
   const int tb = blockIdx.x * per, te = min(A.ntiles, tb + per);
+  const int tx = threadIdx.x % A.tile_x, ty = threadIdx.x / A.tile_x;  // place in the tile
   int cur = -1;
   for (int s = 0; s < A.nsteps; ++s) {
     const int64_t t = t0 + s;
@@ -214,7 +218,7 @@ __global__ void __launch_bounds__(256) k_batch(BatchArgs A) {
       }
       if (!sActive) continue;
       const bool check = check_t && t - A.check_every >= sInit;
-      const int x = T.y + threadIdx.x % A.tile_x, y = T.z + threadIdx.x / A.tile_x;
+      const int x = T.y + tx, y = T.z + ty;
       double acc[kParts] = {0.0, 0.0, 0.0, 0.0, 0.0};
       if (x < sP.nx && y < sP.ny) {
         switch (sI.bc) {
