@@ -314,7 +314,7 @@ def run_ours(args, world, rank, local):
             e2e_steps = max(1, args.steps)
             # host copies on their own stream: the upload of step k+1 and the
             # download of step k overlap with the time steps (ordered by events)
-            lat.set_io_stream(torch.cuda.Stream(dev))
+            lat.set_io_streams(torch.cuda.Stream(dev), torch.cuda.Stream(dev))
             lat.init_host(*h_in).step(lb)
             lat.fields_host(h_out)
             barrier(world)

@@ -153,8 +153,8 @@ ddflb_status ddflb_init(ddflb_ctx* c, const float* rho, const float* ux, const f
                         const float* phi, const float* grads);
 
 /* ddflb_init with HOST input buffers (same layout); the copies run through
- * the input staging area, on the context stream or, after ddflb_set_io_stream,
- * on the I/O stream.  The call does not wait for them: the host buffers must
+ * the input staging area, on the context stream or, after ddflb_set_io_streams,
+ * on the upload stream.  The call does not wait for them: the host buffers must
  * stay valid and unchanged until they are done (ddflb_io_wait, or a
  * synchronisation of the stream that ran them); pinned memory lets the copies
  * overlap with compute.  Requires DDFLB_FLAG_HOST_IO at creation (else EINVAL). */
@@ -210,15 +210,17 @@ ddflb_status ddflb_fields_host(ddflb_ctx* c, float* rho, float* ux, float* uy, f
 ddflb_status ddflb_fields_host_async(ddflb_ctx* c, float* rho, float* ux, float* uy, float* phi,
                                      float* sxx, float* sxy, float* syy, float* omega);
 
-/* Run the host<->device copies of ddflb_init_host / ddflb_fields_host_async on
- * io_stream (a cudaStream_t of the context's device; NULL: back to the context
- * stream), so they overlap with the time steps.  Ordering against the compute
- * stream is kept with events: an upload waits until the previous ddflb_init
- * has consumed the input staging area, ddflb_init waits for its upload, a
- * download waits for its fields kernel, and the next fields kernel waits for
- * the previous download.  This is host-side pipelining only (no paper
+/* Run the uploads of ddflb_init_host on upload_stream and the downloads of
+ * ddflb_fields_host_async on download_stream (two distinct cudaStream_t of
+ * the context's device; both NULL: back to the context stream), so that they
+ * overlap with the time steps and with each other: the upload of step k+1 and
+ * the download of step k run while step k+1 computes.  Ordering against the
+ * compute stream is kept with events: an upload waits until the previous
+ * ddflb_init has consumed the input staging area, ddflb_init waits for its
+ * upload, a download waits for its fields kernel, and the next fields kernel
+ * waits for the previous download.  Host-side pipelining only (no paper
  * counterpart).  Requires DDFLB_FLAG_HOST_IO. */
-ddflb_status ddflb_set_io_stream(ddflb_ctx* c, void* io_stream);
+ddflb_status ddflb_set_io_streams(ddflb_ctx* c, void* upload_stream, void* download_stream);
 
 /* Wait until every host copy queued by this context has completed. */
 ddflb_status ddflb_io_wait(ddflb_ctx* c);

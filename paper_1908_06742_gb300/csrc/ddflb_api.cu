@@ -183,7 +183,7 @@ struct ddflb_ctx {
   int64_t snap_step;  // step at which uprev was last written (-1: none)
   int path;           // step kernel: 0 / 1 one node per thread, 2 paired nodes (16-bit storage)
   float* stage_out;   // output staging area (host I/O)
-  cudaStream_t io;    // stream of the host copies (null: the context stream)
+  cudaStream_t io_up, io_down;  // streams of host uploads / downloads (null: the context stream)
   cudaEvent_t ev_in_free, ev_in_ready, ev_out_ready, ev_out_free;  // host-I/O ordering
 };
 
@@ -327,11 +327,11 @@ ddflb_status ddflb_init(ddflb_ctx* c, const float* rho, const float* ux, const f
   return checks_at(c);
 }
 
-// Host-I/O ordering between the copy stream and the compute stream (no-ops when
+// Host-I/O ordering between a copy stream and the compute stream (no-op when
 // the copies run on the compute stream itself).
-static cudaError_t io_order(ddflb_ctx* c, cudaStream_t waiter, cudaEvent_t ev,
+static cudaError_t io_order(bool separate, cudaStream_t waiter, cudaEvent_t ev,
                             cudaStream_t recorder) {
-  if (!c->io) return cudaSuccess;
+  if (!separate) return cudaSuccess;
   cudaError_t e = cudaEventRecord(ev, recorder);
   return e == cudaSuccess ? cudaStreamWaitEvent(waiter, ev, 0) : e;
 }
@@ -344,9 +344,10 @@ ddflb_status ddflb_init_host(ddflb_ctx* c, const float* rho, const float* ux, co
   const float* src[5] = {rho, ux, uy, phi, grads};
   const size_t planes[5] = {1, 1, 1, 1, 6};
   float* dst[5];
-  cudaStream_t cs = c->io ? c->io : c->L.stream;
+  const bool sep = c->io_up != nullptr;
+  cudaStream_t cs = sep ? c->io_up : c->L.stream;
   // the upload waits until the previous init has read the staging area
-  cudaError_t e = c->io ? cudaStreamWaitEvent(cs, c->ev_in_free, 0) : cudaSuccess;
+  cudaError_t e = sep ? cudaStreamWaitEvent(cs, c->ev_in_free, 0) : cudaSuccess;
   if (e != cudaSuccess) return cuda_fail(e, "init_host order");
   size_t o = 0;
   for (int k = 0; k < 5; ++k) {
@@ -356,11 +357,11 @@ ddflb_status ddflb_init_host(ddflb_ctx* c, const float* rho, const float* ux, co
     e = cudaMemcpyAsync(dst[k], src[k], planes[k] * n * sizeof(float), cudaMemcpyHostToDevice, cs);
     if (e != cudaSuccess) return cuda_fail(e, "init_host copy");
   }
-  e = io_order(c, c->L.stream, c->ev_in_ready, cs);
+  e = io_order(sep, c->L.stream, c->ev_in_ready, cs);
   if (e != cudaSuccess) return cuda_fail(e, "init_host order");
   ddflb_status s = ddflb_init(c, dst[0], dst[1], dst[2], dst[3], grads ? dst[4] : nullptr);
   if (s != DDFLB_OK) return s;
-  e = c->io ? cudaEventRecord(c->ev_in_free, c->L.stream) : cudaSuccess;
+  e = sep ? cudaEventRecord(c->ev_in_free, c->L.stream) : cudaSuccess;
   return e == cudaSuccess ? DDFLB_OK : cuda_fail(e, "init_host order");
 }
 
@@ -410,22 +411,23 @@ ddflb_status ddflb_fields_host_async(ddflb_ctx* c, float* rho, float* ux, float*
   float* host[8] = {rho, ux, uy, phi, sxx, sxy, syy, omega};
   FieldPtrs fp{};
   for (int k = 0; k < 8; ++k) fp.p[k] = host[k] ? c->stage_out + k * n : nullptr;
-  cudaStream_t cs = c->io ? c->io : c->L.stream;
+  const bool sep = c->io_down != nullptr;
+  cudaStream_t cs = sep ? c->io_down : c->L.stream;
   // the fields kernel waits until the previous download has drained the staging area
-  cudaError_t e = c->io ? cudaStreamWaitEvent(c->L.stream, c->ev_out_free, 0) : cudaSuccess;
+  cudaError_t e = sep ? cudaStreamWaitEvent(c->L.stream, c->ev_out_free, 0) : cudaSuccess;
   if (e != cudaSuccess) return cuda_fail(e, "fields_host order");
   at_time(c, c->step);
   ddflb_status s =
       check_launch(launch_fields(c->L, fptr(c, c->cur), gptr(c, c->cur), fp), "fields_host");
   if (s != DDFLB_OK) return s;
-  e = io_order(c, cs, c->ev_out_ready, c->L.stream);
+  e = io_order(sep, cs, c->ev_out_ready, c->L.stream);
   if (e != cudaSuccess) return cuda_fail(e, "fields_host order");
   for (int k = 0; k < 8; ++k) {
     if (!host[k]) continue;
     e = cudaMemcpyAsync(host[k], fp.p[k], n * sizeof(float), cudaMemcpyDeviceToHost, cs);
     if (e != cudaSuccess) return cuda_fail(e, "fields_host copy");
   }
-  e = c->io ? cudaEventRecord(c->ev_out_free, cs) : cudaSuccess;
+  e = sep ? cudaEventRecord(c->ev_out_free, cs) : cudaSuccess;
   return e == cudaSuccess ? DDFLB_OK : cuda_fail(e, "fields_host order");
 }
 
@@ -437,14 +439,18 @@ ddflb_status ddflb_fields_host(ddflb_ctx* c, float* rho, float* ux, float* uy, f
 
 ddflb_status ddflb_io_wait(ddflb_ctx* c) {
   if (!c) return fail(DDFLB_EINVAL, "NULL handle");
-  cudaError_t e = cudaStreamSynchronize(c->io ? c->io : c->L.stream);
+  cudaError_t e = cudaStreamSynchronize(c->io_up ? c->io_up : c->L.stream);
+  if (e == cudaSuccess && c->io_down) e = cudaStreamSynchronize(c->io_down);
   return e == cudaSuccess ? DDFLB_OK : cuda_fail(e, "io_wait");
 }
 
-ddflb_status ddflb_set_io_stream(ddflb_ctx* c, void* io_stream) {
+ddflb_status ddflb_set_io_streams(ddflb_ctx* c, void* upload_stream, void* download_stream) {
   if (!c) return fail(DDFLB_EINVAL, "NULL handle");
   if (!c->stage) return fail(DDFLB_EINVAL, "context created without DDFLB_FLAG_HOST_IO");
-  if (io_stream && !c->ev_in_free) {
+  if ((upload_stream == nullptr) != (download_stream == nullptr) ||
+      (upload_stream && upload_stream == download_stream))
+    return fail(DDFLB_EINVAL, "give two distinct I/O streams, or none");
+  if (upload_stream && !c->ev_in_free) {
     cudaEvent_t* evs[4] = {&c->ev_in_free, &c->ev_in_ready, &c->ev_out_ready, &c->ev_out_free};
     for (cudaEvent_t* ev : evs) {
       cudaError_t e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
@@ -452,9 +458,10 @@ ddflb_status ddflb_set_io_stream(ddflb_ctx* c, void* io_stream) {
     }
   }
   // copies queued so far complete before the streams change roles
-  cudaError_t e = cudaStreamSynchronize(c->io ? c->io : c->L.stream);
-  if (e != cudaSuccess) return cuda_fail(e, "set_io_stream");
-  c->io = (cudaStream_t)io_stream;
+  ddflb_status s = ddflb_io_wait(c);
+  if (s != DDFLB_OK) return s;
+  c->io_up = (cudaStream_t)upload_stream;
+  c->io_down = (cudaStream_t)download_stream;
   return DDFLB_OK;
 }
 

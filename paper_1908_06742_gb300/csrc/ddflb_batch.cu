@@ -129,13 +129,19 @@ __device__ bool grid_barrier(BatchSync* s, long long timeout_ns) {
 
 template <typename S, int BC>
 __device__ __forceinline__ void batch_cell(const LbParams& P, const BatchInst& I, int src, int x,
-                                           int y, bool snap, bool check, double acc[kParts]) {
+                                           int y, bool inner, bool snap, bool check,
+                                           double acc[kParts]) {
   const S* fin = (const S*)I.buf[src];
   const S* gin = fin + I.goff;
   S* fout = (S*)I.buf[src ^ 1];
   S* gout = fout + I.goff;
   float df[9], dg[9];
-  pull<S, BC>(P, fin, gin, x, y, df, dg);
+  // a warp whose nodes all have their 8 neighbours inside the lattice pulls
+  // without the wall rules (same addresses, so the same values)
+  if (BC != BC_PERIODIC && inner)
+    pull<S, BC_PERIODIC>(P, fin, gin, x, y, df, dg);
+  else
+    pull<S, BC>(P, fin, gin, x, y, df, dg);
   const Mom mf = moments_flow(df), mg = moments_scalar(dg);
   const Macro q = macro(P, mf, mg);
   relax(P.wf, neq_flow(mf, q), df);
@@ -220,11 +226,19 @@ __global__ void __launch_bounds__(256, 4) k_batch(BatchArgs A) {
       const bool check = check_t && t - A.check_every >= sInit;
       const int x = T.y + tx, y = T.z + ty;
       double acc[kParts] = {0.0, 0.0, 0.0, 0.0, 0.0};
+      // warp-uniform (all lanes vote, before any lane drops out); the channel is
+      // periodic in x, so only its walls in y count
+      const bool in_x = sI.bc == BC_CHANNEL ? x < sP.nx : (x >= 1 && x < sP.nx - 1);
+      const bool inner = __all_sync(0xffffffffu, in_x && y >= 1 && y < sP.ny - 1);
       if (x < sP.nx && y < sP.ny) {
         switch (sI.bc) {
-          case BC_PERIODIC: batch_cell<S, BC_PERIODIC>(sP, sI, src, x, y, snap, check, acc); break;
-          case BC_CAVITY: batch_cell<S, BC_CAVITY>(sP, sI, src, x, y, snap, check, acc); break;
-          default: batch_cell<S, BC_CHANNEL>(sP, sI, src, x, y, snap, check, acc);
+          case BC_PERIODIC:
+            batch_cell<S, BC_PERIODIC>(sP, sI, src, x, y, inner, snap, check, acc);
+            break;
+          case BC_CAVITY:
+            batch_cell<S, BC_CAVITY>(sP, sI, src, x, y, inner, snap, check, acc);
+            break;
+          default: batch_cell<S, BC_CHANNEL>(sP, sI, src, x, y, inner, snap, check, acc);
         }
       }
       if (check) {

@@ -28,10 +28,21 @@ __global__ void __launch_bounds__(256) k_step(LbParams P, const S* __restrict__ 
                                               const DevStatus* __restrict__ status) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  // with walls: a warp (32 consecutive x of one row) whose nodes all have their
+  // neighbours inside the lattice pulls without the wall rules (same addresses,
+  // same values); decided by a vote of all lanes before any returns
+  bool inner = false;
+  if (BC != BC_PERIODIC) {
+    const bool in_x = BC == BC_CHANNEL ? x < P.nx : (x >= 1 && x < P.nx - 1);
+    inner = __all_sync(0xffffffffu, in_x && y >= 1 && y < P.ny - 1);
+  }
   if (x >= P.nx || y >= P.ny) return;
   if (status != nullptr && status->diverged) return;
   float df[9], dg[9];
-  pull<S, BC>(P, fin, gin, x, y, df, dg);
+  if (BC != BC_PERIODIC && inner)
+    pull<S, BC_PERIODIC>(P, fin, gin, x, y, df, dg);
+  else
+    pull<S, BC>(P, fin, gin, x, y, df, dg);
   collide<FORCE, SM>(P, x, y, df, dg);
   const int64_t o = (int64_t)y * P.pitch + x;
 #pragma unroll

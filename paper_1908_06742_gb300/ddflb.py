@@ -67,7 +67,7 @@ SIGNATURES = {
     "ddflb_fields_host": (ctypes.c_int, [_VP] + [_FP] * 8),
     "ddflb_derived": (ctypes.c_int, [_VP] + [_FP] * 10),
     "ddflb_fields_host_async": (ctypes.c_int, [_VP] + [_FP] * 8),
-    "ddflb_set_io_stream": (ctypes.c_int, [_VP, _VP]),
+    "ddflb_set_io_streams": (ctypes.c_int, [_VP, _VP, _VP]),
     "ddflb_io_wait": (ctypes.c_int, [_VP]),
     "ddflb_populations": (ctypes.c_int, [_VP, _FP, _FP]),
     "ddflb_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
@@ -319,10 +319,13 @@ class Lattice:
             self._h, *[(out[k].data_ptr() if k in out else None) for k in FIELD_NAMES]))
         return out
 
-    def set_io_stream(self, stream):
-        """Run host copies on ``stream`` (a torch.cuda.Stream; None: the context stream)."""
-        self._io = stream
-        _check(self.lib.ddflb_set_io_stream(self._h, None if stream is None else stream.cuda_stream))
+    def set_io_streams(self, upload=None, download=None):
+        """Run host uploads / downloads on two torch.cuda.Streams (None, None: the
+        context stream), overlapping them with the time steps."""
+        self._io = (upload, download)
+        _check(self.lib.ddflb_set_io_streams(
+            self._h, None if upload is None else upload.cuda_stream,
+            None if download is None else download.cuda_stream))
         return self
 
     def io_wait(self):

@@ -72,7 +72,7 @@ def test_pipelined_host_io_matches_synchronous():
         out = {k: torch.empty((n, n)).pin_memory() for k in D.FIELD_NAMES}
         a.init_host(*h).step(steps).fields_host(out)
         ref.append({k: v.clone() for k, v in out.items()})
-    b = D.Lattice(cfg).set_io_stream(torch.cuda.Stream())
+    b = D.Lattice(cfg).set_io_streams(torch.cuda.Stream(), torch.cuda.Stream())
     outs = [{k: torch.empty((n, n)).pin_memory() for k in D.FIELD_NAMES} for _ in ins]
     for h, out in zip(ins, outs):
         b.init_host(*h).step(steps).fields_host_async(out)
