@@ -6,8 +6,8 @@ and the node coordinates to the steady fields (u_x, u_y, phi, omega, and the
 density rho for a consistent pressure).  The prediction only initialises the
 populations -- equilibrium plus the Chapman-Enskog non-equilibrium part implied
 by the predicted gradients -- and the lattice Boltzmann method then runs to the
-residual tolerance exactly as from a cold start, so the method stays the judge
-of the surrogate.  Training data are steady solutions the method itself
+residual tolerance exactly as from a cold start, so the method, not the
+network, decides the final state.  Training data are steady solutions the method itself
 produces (batched runs to the tolerance).
 
 Every arithmetic step runs in libddflb's kernels (tensor-core GEMM, im2col,

@@ -1,7 +1,7 @@
 """What the trained network gains over the method without it: held-out
 cavities reach the residual tolerance in fewer steps from the network's
 prediction than from rest, and converge to the same vorticity.  The method
-remains the judge: both runs stop only at residual 1e-8 (velocity and scalar).
+decides the final state: both runs stop only at residual 1e-8 (velocity and scalar).
 Small configuration (64^2 grid, 192 training cavities) so the test runs in
 well under a minute."""
 import pytest
