@@ -576,8 +576,9 @@ GEMM_SHAPES = [(262144, 32, 144, 1), (65536, 64, 288, 1), (16384, 128, 576, 1),
 
 
 def run_gemm(args, world, rank, local):
-    """BF16 GEMM throughput of the surrogate's contraction shapes on both
-    tensor-core paths (0: tcgen05 + TMA, 1: mma.sync), CUDA events per shape."""
+    """BF16 GEMM throughput of the surrogate's contraction shapes on the
+    tensor-core paths (0: tcgen05 + TMA, persistent; 1: mma.sync; 2: tcgen05,
+    one tile per CTA), CUDA events per shape."""
     import torch
     from paper_1908_06742_gb300 import build as B
     from paper_1908_06742_gb300 import ddflb as D
@@ -587,7 +588,7 @@ def run_gemm(args, world, rank, local):
     shapes = GEMM_SHAPES
     if args.gemm_shape:
         shapes = [tuple(int(v) for v in args.gemm_shape.split(","))]
-    rows, tot = [], {0: [0.0, 0.0], 1: [0.0, 0.0]}
+    rows, tot = [], {0: [0.0, 0.0], 1: [0.0, 0.0], 2: [0.0, 0.0]}
     st = torch.cuda.current_stream()
     for M, N, K, sp in shapes:
         g = torch.Generator(device="cuda").manual_seed(M + N + K)
@@ -596,7 +597,7 @@ def run_gemm(args, world, rank, local):
         C = torch.empty(M, N, device="cuda")
         part = torch.empty(sp * M * N, device="cuda") if sp > 1 else None
         row = {"M": M, "N": N, "K": K, "splits": sp}
-        for path in (0, 1):
+        for path in (0, 1, 2):
             D._check(lib.ddflb_nn_set_gemm_path(path))
 
             def call():
@@ -637,10 +638,12 @@ def run_gemm(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": round(tot[0][1], 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": "U-Net convolution GEMMs (forward and weight-gradient shapes)",
-                   "kernel": "tcgen05 + TMA (path 0); mma.sync reference (path 1)"},
+                   "kernel": "tcgen05 + TMA persistent (path 0); mma.sync (path 1); "
+                             "tcgen05 one tile per CTA (path 2)"},
         "roofline": {"bound": "tensor", "achieved": round(agg[0], 1), "peak": peak,
                      "unit": "TFLOP/s", "frac": round(agg[0] / peak, 4), "peak_kind": kind},
-        "mma_sync_tflops": round(agg[1], 1), "device_error_word": err.value, "shapes": rows}))
+        "mma_sync_tflops": round(agg[1], 1), "tcgen05_tile_per_cta_tflops": round(agg[2], 1),
+        "device_error_word": err.value, "shapes": rows}))
 
 
 def main():

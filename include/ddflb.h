@@ -380,11 +380,15 @@ ddflb_status ddflb_nn_gemm(const void* A, const void* B, int32_t M, int32_t N, i
                            int32_t lda, int32_t ldb, float* Cf, int32_t ldc, void* Cb,
                            int32_t ldcb, const float* bias, int32_t act, int32_t accumulate,
                            int32_t splits, float* partial, void* stream);
-/* GEMM kernel for all later ddflb_nn_gemm calls of the process: 0 (default) =
- * tcgen05 (TMA-fed ring of 128-byte-swizzled shared-memory slots, one thread
- * issues the MMAs, FP32 accumulator in tensor memory, 128 x {32, 64, 128}
- * tiles), 1 = mma.sync m16n8k16 (register accumulators).  Same results up to
- * the order of FP32 additions. */
+/* GEMM kernel for all later ddflb_nn_gemm calls of the process:
+ *  0 (default) = tcgen05, persistent when there are more 128 x {32, 64, 128}
+ *    tiles than SMs (one CTA per SM walks the tiles; a TMA warp fills a ring of
+ *    128-byte-swizzled shared-memory slots, one thread issues the MMAs into two
+ *    alternating FP32 accumulators in tensor memory, four warps run the
+ *    epilogue of the previous tile meanwhile), otherwise as path 2;
+ *  1 = mma.sync m16n8k16 (register accumulators);
+ *  2 = tcgen05 with one tile per CTA.
+ * Same results up to the order of FP32 additions. */
 ddflb_status ddflb_nn_set_gemm_path(int32_t path);
 /* Copy to *error and clear the tcgen05 GEMM's device error word (1 = a bounded
  * wait ran out and a tile was skipped; 0 = none).  Synchronises `stream`. */

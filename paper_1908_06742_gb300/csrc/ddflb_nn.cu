@@ -270,6 +270,66 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t r[32]) {
 }
 #undef DDFLB_R8
 
+// Epilogue of one accumulator row segment: 32 FP32 columns (cb .. cb+31) of
+// row r, plus bias and activation, to the split-K partial buffer (slice z), the
+// FP32 output (optionally accumulated) and/or the BF16 output; 16-byte stores
+// where the layout allows (vf, vb).
+__device__ __forceinline__ void store_row32(const GemmArgs& g, int r, int cb, int z,
+                                            const uint32_t v[32], bool has_k, bool vf, bool vb) {
+  float x[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    float t = has_k ? __uint_as_float(v[i]) : 0.0f;
+    if (!g.partial) {
+      if (g.bias && cb + i < g.N) t += g.bias[cb + i];
+      t = act_fwd(t, g.act);
+    }
+    x[i] = t;
+  }
+  if (g.partial) {
+    float* p = g.partial + ((size_t)z * g.M + r) * g.N;
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+      if (cb + i < g.N) p[cb + i] = x[i];
+    return;
+  }
+  const bool full_chunk = cb + 32 <= g.N;
+  if (g.Cf) {
+    float* p = g.Cf + (size_t)r * g.ldc + cb;
+    if (vf && full_chunk) {
+#pragma unroll
+      for (int i = 0; i < 32; i += 4) {
+        float4 o = make_float4(x[i], x[i + 1], x[i + 2], x[i + 3]);
+        if (g.accumulate) {
+          const float4 q = *reinterpret_cast<const float4*>(p + i);
+          o.x += q.x; o.y += q.y; o.z += q.z; o.w += q.w;
+        }
+        *reinterpret_cast<float4*>(p + i) = o;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 32; ++i)
+        if (cb + i < g.N) p[i] = g.accumulate ? p[i] + x[i] : x[i];
+    }
+  }
+  if (g.Cb) {
+    bf16* p = g.Cb + (size_t)r * g.ldcb + cb;
+    if (vb && full_chunk) {
+#pragma unroll
+      for (int i = 0; i < 32; i += 8) {
+        __align__(16) bf16 h[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) h[e] = __float2bfloat16_rn(x[i + e]);
+        *reinterpret_cast<uint4*>(p + i) = *reinterpret_cast<const uint4*>(h);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 32; ++i)
+        if (cb + i < g.N) p[i] = __float2bfloat16_rn(x[i]);
+    }
+  }
+}
+
 template <int BN>
 __global__ void __launch_bounds__(tc::THREADS) k_gemm_tc(const __grid_constant__ CUtensorMap tmA,
                                                          const __grid_constant__ CUtensorMap tmB,
@@ -386,60 +446,256 @@ __global__ void __launch_bounds__(tc::THREADS) k_gemm_tc(const __grid_constant__
       uint32_t v[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
       if (r >= g.M) continue;
-      const int cb = n0 + c0;
-      float x[32];
-#pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        float t = nk > 0 ? __uint_as_float(v[i]) : 0.0f;
-        if (!g.partial) {
-          if (g.bias && cb + i < g.N) t += g.bias[cb + i];
-          t = act_fwd(t, g.act);
-        }
-        x[i] = t;
-      }
-      if (g.partial) {
-        float* p = g.partial + ((size_t)blockIdx.z * g.M + r) * g.N;
-#pragma unroll
-        for (int i = 0; i < 32; ++i)
-          if (cb + i < g.N) p[cb + i] = x[i];
-        continue;
-      }
-      const bool full_chunk = cb + 32 <= g.N;
-      if (g.Cf) {
-        float* p = g.Cf + (size_t)r * g.ldc + cb;
-        if (vf && full_chunk) {
-#pragma unroll
-          for (int i = 0; i < 32; i += 4) {
-            float4 o = make_float4(x[i], x[i + 1], x[i + 2], x[i + 3]);
-            if (g.accumulate) {
-              const float4 q = *reinterpret_cast<const float4*>(p + i);
-              o.x += q.x; o.y += q.y; o.z += q.z; o.w += q.w;
-            }
-            *reinterpret_cast<float4*>(p + i) = o;
-          }
-        } else {
-#pragma unroll
-          for (int i = 0; i < 32; ++i)
-            if (cb + i < g.N) p[i] = g.accumulate ? p[i] + x[i] : x[i];
-        }
-      }
-      if (g.Cb) {
-        bf16* p = g.Cb + (size_t)r * g.ldcb + cb;
-        if (vb && full_chunk) {
-#pragma unroll
-          for (int i = 0; i < 32; i += 8) {
-            __align__(16) bf16 h[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) h[e] = __float2bfloat16_rn(x[i + e]);
-            *reinterpret_cast<uint4*>(p + i) = *reinterpret_cast<const uint4*>(h);
-          }
-        } else {
-#pragma unroll
-          for (int i = 0; i < 32; ++i)
-            if (cb + i < g.N) p[i] = __float2bfloat16_rn(x[i]);
-        }
-      }
+      store_row32(g, r, n0 + c0, blockIdx.z, v, nk > 0, vf, vb);
     }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(C::COLS)
+                 : "memory");
+  }
+}
+
+// Persistent form (the default): one CTA per SM walks the tiles (z, m, n) with
+// stride gridDim.x, in 6 warps with fixed roles, so that the loads and MMAs of
+// the next tile overlap the epilogue of the previous one:
+//  - warp 0 (one thread): TMA producer over a ring of STAGES slots, as above,
+//    the slot/phase counters running on across tiles;
+//  - warp 1 (one thread): MMA issuer into one of two accumulators in tensor
+//    memory (columns [0, BN) and [BN, 2 BN)), alternating per tile; before
+//    reusing one it waits on that accumulator's `tmem_empty` mbarrier, and
+//    after a tile's last MMA it commits to its `tmem_full`;
+//  - warps 2-5 (the epilogue): wait on `tmem_full`, read their lane quarter
+//    (warp w reads lanes 32 (w mod 4) .. +31) with tcgen05.ld, store, and free
+//    the accumulator (one arrival on `tmem_empty` after a named barrier).
+// Every wait is bounded and also ends when another role has given up (a
+// shared flag); the CTA then records the error, lets its copies in flight land
+// (bounded), frees its tensor memory and returns.
+namespace tcp {
+constexpr int THREADS = 192;
+template <int BN>
+struct Cfg {
+  using T = tc::Cfg<BN>;
+  static constexpr int STAGES = T::STAGES;
+  static constexpr int STAGE = T::STAGE;
+  static constexpr int SMEM = STAGES * STAGE + 1024 + 512;
+  static constexpr uint32_t COLS = 2 * BN < 32 ? 32 : 2 * BN;  // two accumulators
+};
+}  // namespace tcp
+
+// bounded wait that also gives up once *abort is set
+__device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, uint32_t parity,
+                                             const volatile int* abort) {
+  const uint64_t deadline = globaltimer_ns() + 1000000000ull;
+  for (uint32_t it = 0; it < (1u << 24); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 255) == 255 && (*abort || globaltimer_ns() > deadline)) return false;
+  }
+  return false;
+}
+
+template <int BN>
+__global__ void __launch_bounds__(tcp::THREADS, 1) k_gemm_tcp(
+    const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmArgs g,
+    int tiles_m, int tiles_n, int tiles_z) {
+  using C = tcp::Cfg<BN>;
+  using T = tc::Cfg<BN>;
+  constexpr int S = C::STAGES;
+  extern __shared__ uint8_t dsmem[];
+  __shared__ int s_abort;
+  __shared__ int s_issued, s_consumed;  // k-steps requested by the producer / read by the MMAs
+  __shared__ int s_ep_ok[4];            // per epilogue warp: its accumulator wait succeeded
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t raw = smem_u32(dsmem);
+  const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(dsmem + pad + S * C::STAGE);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * S + 5);
+  const uint32_t tiles_u = raw + pad;
+  const uint32_t full_u = smem_u32(bars), empty_u = full_u + 8 * S;
+  const uint32_t tfull_u = full_u + 16 * S, tempty_u = tfull_u + 16;  // two of each
+  const uint32_t mdone_u = tempty_u + 16;  // the MMA thread's last commit
+  const volatile int* abort = &s_abort;
+
+  if (tid == 0) {
+    s_abort = 0;
+    s_issued = 0;
+    s_consumed = 0;
+    for (int i = 0; i < S; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full_u + 8 * i) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(empty_u + 8 * i) : "memory");
+    }
+    for (int i = 0; i < 2; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tfull_u + 8 * i) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tempty_u + 8 * i) : "memory");
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mdone_u) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tslot)),
+                 "r"(C::COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const int ntiles = tiles_m * tiles_n * tiles_z;
+  // tile t -> (z, m, n), n fastest: neighbouring CTAs share the A tile in L2
+  auto coords = [&](int t, int& m0, int& n0, int& kbeg, int& nk) {
+    const int n = t % tiles_n, m = (t / tiles_n) % tiles_m, z = t / (tiles_n * tiles_m);
+    m0 = m * tc::BM;
+    n0 = n * BN;
+    kbeg = z * g.kchunk;
+    const int kend = min(g.K, kbeg + g.kchunk);
+    nk = kend > kbeg ? (kend - kbeg + tc::BK - 1) / tc::BK : 0;
+    return z;
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- producer
+      int gk = 0;  // k-steps issued so far (all tiles)
+      for (int t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x) {
+        int m0, n0, kbeg, nk;
+        coords(t, m0, n0, kbeg, nk);
+        for (int kt = 0; kt < nk; ++kt, ++gk) {
+          const int st = gk % S;
+          if (gk >= S && !mbar_wait_ab(empty_u + 8 * st, ((gk / S) - 1) & 1, abort)) {
+            s_abort = 1;
+            break;
+          }
+          const uint32_t bar = full_u + 8 * st;
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                       "r"(C::STAGE)
+                       : "memory");
+          const uint32_t sa = tiles_u + st * C::STAGE;
+          const int k0 = kbeg + kt * tc::BK;  // a multiple of 64 elements (128 B)
+          tma_2d(sa, &tmA, k0, m0, bar);
+          tma_2d(sa + T::A_TILE, &tmB, k0, n0, bar);
+        }
+      }
+      s_issued = gk;
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      int gk = 0, it = 0;
+      for (int t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x, ++it) {
+        int m0, n0, kbeg, nk;
+        coords(t, m0, n0, kbeg, nk);
+        const int acc = it & 1;
+        // the epilogue of tile it - 2 has read this accumulator
+        if (it >= 2 && !mbar_wait_ab(tempty_u + 8 * acc, ((it >> 1) - 1) & 1, abort)) {
+          s_abort = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(acc * BN);
+        bool ok = true;
+        for (int kt = 0; kt < nk; ++kt, ++gk) {
+          const int st = gk % S;
+          if (!mbar_wait_ab(full_u + 8 * st, (gk / S) & 1, abort)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = tiles_u + st * C::STAGE, b0 = a0 + T::A_TILE;
+#pragma unroll
+          for (int kk = 0; kk < tc::BK / 16; ++kk) {
+            const uint64_t ad = smem_desc_sw128(a0 + kk * 32, T::SBO);
+            const uint64_t bd = smem_desc_sw128(b0 + kk * 32, T::SBO);
+            const uint32_t accum = (kt > 0 || kk > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                "l"(ad), "l"(bd), "r"(T::IDESC), "r"(accum)
+                : "memory");
+          }
+          asm volatile(
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                  empty_u + 8 * st)
+              : "memory");
+        }
+        if (!ok) {
+          s_abort = 1;
+          break;
+        }
+        // the accumulator is complete once these MMAs are
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                tfull_u + 8 * acc)
+            : "memory");
+      }
+      s_consumed = gk;
+      // every MMA this thread issued has completed before the CTA moves on
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              mdone_u)
+          : "memory");
+      if (!mbar_wait(mdone_u, 0)) s_abort = 1;
+    }
+  } else {
+    // ---------------- epilogue, warps 2-5: lane quarter q = warp mod 4
+    const int q = warp & 3;
+    const bool vf = g.Cf && !g.partial && (g.ldc & 3) == 0 && ((uintptr_t)g.Cf & 15) == 0;
+    const bool vb = g.Cb && !g.partial && (g.ldcb & 7) == 0 && ((uintptr_t)g.Cb & 15) == 0;
+    int it = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+      int m0, n0, kbeg, nk;
+      const int z = coords(t, m0, n0, kbeg, nk);
+      const int acc = it & 1;
+      int ready = 1;
+      if (lane == 0) ready = mbar_wait_ab(tfull_u + 8 * acc, (it >> 1) & 1, abort) ? 1 : 0;
+      ready = __shfl_sync(0xffffffffu, ready, 0);
+      // the four epilogue warps decide together (no warp leaves the named barrier alone)
+      if (lane == 0) s_ep_ok[q] = ready;
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      const int all_ok = s_ep_ok[0] & s_ep_ok[1] & s_ep_ok[2] & s_ep_ok[3];
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (!all_ok) {
+        if (warp == 2 && lane == 0) s_abort = 1;
+        break;
+      }
+      tc_fence_after();
+      const int r = m0 + q * 32 + lane;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t v[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c0), v);
+        if (r < g.M) store_row32(g, r, n0 + c0, z, v, nk > 0, vf, vb);
+      }
+      // all four epilogue warps are done with this accumulator
+      tc_fence_before();
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (warp == 2 && lane == 0)
+        asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(tempty_u + 8 * acc)
+                     : "memory");
+    }
+  }
+  __syncwarp();
+  __syncthreads();
+  if (s_abort) {
+    if (tid == 0) {
+      atomicExch(&g_tc_error, 1);
+      // let the copies still in flight land before the CTA's memory goes away
+      for (int k2 = s_consumed; k2 < s_issued; ++k2)
+        mbar_wait(full_u + 8 * (k2 % S), (k2 / S) & 1);
+    }
+    __syncthreads();
   }
   tc_fence_before();
   __syncthreads();
@@ -822,7 +1078,7 @@ ddflb_status bad(const char* msg) {
 }  // namespace
 
 namespace {
-int g_gemm_path = 0;  // 0: tcgen05 kernel (default), 1: mma.sync kernel
+int g_gemm_path = 0;  // 0: tcgen05 persistent (default), 1: mma.sync, 2: tcgen05 one tile per CTA
 
 // cuTensorMapEncodeTiled from the driver, looked up through the runtime (no
 // link-time dependency on the driver library)
@@ -859,6 +1115,35 @@ bool make_map(CUtensorMap* m, const void* base, int rows, int K, int ld, int box
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+      n = 1;
+  }
+  return n;
+}
+
+template <int BN>
+ddflb_status gemm_tcp_bn(const GemmArgs& g, int tm, int tn, int tz, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_gemm_tcp<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             tcp::Cfg<BN>::SMEM) != cudaSuccess)
+      return launched("gemm tcgen05 attribute");
+    attr = true;
+  }
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, g.A, g.M, g.K, g.lda, tc::BM) || !make_map(&mb, g.B, g.N, g.K, g.ldb, BN))
+    return bad("gemm: TMA tensor map encoding failed");
+  const int ntiles = tm * tn * tz;
+  const int grid = ntiles < sm_count() ? ntiles : sm_count();
+  k_gemm_tcp<BN><<<grid, tcp::THREADS, tcp::Cfg<BN>::SMEM, s>>>(ma, mb, g, tm, tn, tz);
+  return launched("gemm tcgen05 persistent");
+}
+
 template <int BN>
 ddflb_status gemm_tc_bn(const GemmArgs& g, dim3 grid, cudaStream_t s) {
   static bool attr = false;
@@ -876,7 +1161,7 @@ ddflb_status gemm_tc_bn(const GemmArgs& g, dim3 grid, cudaStream_t s) {
 }
 
 // N tile: the smallest of 32, 64, 128 that covers N (wider N: 128-column tiles)
-ddflb_status gemm_tc(GemmArgs g, int splits, cudaStream_t s) {
+ddflb_status gemm_tc(GemmArgs g, int splits, bool persistent, cudaStream_t s) {
   int kchunk = g.K;
   if (splits > 1) {
     kchunk = (g.K + splits - 1) / splits;
@@ -886,9 +1171,17 @@ ddflb_status gemm_tc(GemmArgs g, int splits, cudaStream_t s) {
   g.kchunk = kchunk;
   const int bn = g.N <= 32 ? 32 : g.N <= 64 ? 64 : 128;
   dim3 grid((g.N + bn - 1) / bn, (g.M + tc::BM - 1) / tc::BM, z);
-  ddflb_status st = bn == 32   ? gemm_tc_bn<32>(g, grid, s)
-                    : bn == 64 ? gemm_tc_bn<64>(g, grid, s)
-                               : gemm_tc_bn<128>(g, grid, s);
+  ddflb_status st;
+  // with no more tiles than SMs every CTA would own one tile anyway: the
+  // one-tile kernel has the lighter set-up
+  if (persistent && (int64_t)grid.x * grid.y * grid.z > sm_count())
+    st = bn == 32   ? gemm_tcp_bn<32>(g, grid.y, grid.x, z, s)
+         : bn == 64 ? gemm_tcp_bn<64>(g, grid.y, grid.x, z, s)
+                    : gemm_tcp_bn<128>(g, grid.y, grid.x, z, s);
+  else
+    st = bn == 32   ? gemm_tc_bn<32>(g, grid, s)
+         : bn == 64 ? gemm_tc_bn<64>(g, grid, s)
+                    : gemm_tc_bn<128>(g, grid, s);
   if (st != DDFLB_OK || splits == 1) return st;
   k_splitk_reduce<<<grid_for((int64_t)g.M * g.N), 256, 0, s>>>(g.partial, z, g.M, g.N, g.Cf, g.ldc,
                                                                g.bias, g.act, g.accumulate);
@@ -899,7 +1192,8 @@ ddflb_status gemm_tc(GemmArgs g, int splits, cudaStream_t s) {
 extern "C" {
 
 ddflb_status ddflb_nn_set_gemm_path(int32_t path) {
-  if (path < 0 || path > 1) return bad("gemm path must be 0 (tcgen05) or 1 (mma.sync)");
+  if (path < 0 || path > 2)
+    return bad("gemm path must be 0 (tcgen05 persistent), 1 (mma.sync) or 2 (tcgen05, one tile per CTA)");
   g_gemm_path = path;
   return DDFLB_OK;
 }
@@ -933,12 +1227,12 @@ ddflb_status ddflb_nn_gemm(const void* A, const void* B, int32_t M, int32_t N, i
   cudaStream_t s = (cudaStream_t)stream;
   if (splits > 1 && (!Cf || Cb || !partial))
     return bad("gemm: split-K needs Cf and partial (and no Cb)");
-  if (g_gemm_path == 0) {
+  if (g_gemm_path == 0 || g_gemm_path == 2) {
     GemmArgs g{(const bf16*)A, (const bf16*)B, M, N, K, lda, ldb, splits > 1 ? nullptr : Cf,
                splits > 1 ? nullptr : (bf16*)Cb, ldc, ldcb, bias, act, accumulate, K,
                splits > 1 ? partial : nullptr};
     if (splits > 1) g.Cf = Cf;  // read by the split-K reduction only
-    return gemm_tc(g, splits, s);
+    return gemm_tc(g, splits, g_gemm_path == 0, s);
   }
   if (splits == 1) {
     GemmArgs g{(const bf16*)A, (const bf16*)B, M, N, K, lda, ldb, Cf, (bf16*)Cb, ldc, ldcb,

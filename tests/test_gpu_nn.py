@@ -44,14 +44,17 @@ def take_error():
     return e.value
 
 
-@pytest.mark.parametrize("path", [0, 1])
+@pytest.mark.parametrize("path", [0, 1, 2])
 @pytest.mark.parametrize("M,N,K,splits,bias,act", [
     (1, 1, 8, 1, False, 0), (130, 70, 40, 1, True, 1), (257, 129, 136, 1, True, 0),
     (1000, 64, 4096, 7, False, 0), (64, 2304, 8192, 16, True, 1), (300, 8, 32, 1, True, 0),
-    (4096, 128, 576, 1, True, 1), (513, 256, 1152, 3, False, 0)])
+    (4096, 128, 576, 1, True, 1), (513, 256, 1152, 3, False, 0),
+    # more tiles than SMs (the persistent kernel), ragged in M, N and K
+    (40000, 96, 200, 1, True, 1), (20000, 32, 72, 1, False, 0), (1300, 64, 8192, 16, False, 0)])
 def test_gemm_against_float64(M, N, K, splits, bias, act, path, gemm_path):
-    """Both GEMM kernels (0: tcgen05, 1: mma.sync) against a float64 product of
-    the same BF16 operands, over ragged multi-tile shapes and split-K."""
+    """The GEMM kernels (0: tcgen05 persistent, 1: mma.sync, 2: tcgen05 one
+    tile per CTA) against a float64 product of the same BF16 operands, over
+    ragged multi-tile shapes and split-K."""
     gemm_path(path)
     g = torch.Generator().manual_seed(M * 7 + N)
     A = torch.randn(M, K, generator=g).to(torch.bfloat16).cuda()
@@ -81,7 +84,7 @@ def test_gemm_against_float64(M, N, K, splits, bias, act, path, gemm_path):
     assert take_error() == 0
 
 
-@pytest.mark.parametrize("path", [0, 1])
+@pytest.mark.parametrize("path", [0, 1, 2])
 def test_gemm_accumulate_and_strides(path, gemm_path):
     """accumulate = 1 adds to Cf; lda, ldb, ldc larger than K and N."""
     gemm_path(path)
