@@ -74,8 +74,9 @@ ddflb_status validate(const ddflb_params* p) {
   if (p->bc < 0 || p->bc > 2) return fail(DDFLB_EINVAL, "bc %d is not a ddflb_bc", p->bc);
   const int minx = p->bc == DDFLB_BC_CHANNEL ? 1 : 2;
   if (p->nx < minx || p->ny < 2) return fail(DDFLB_EINVAL, "grid %d x %d too small", p->nx, p->ny);
-  if ((int64_t)p->nx * p->ny > (int64_t)1 << 32)
-    return fail(DDFLB_EINVAL, "grid %d x %d exceeds 2^32 nodes", p->nx, p->ny);
+  // a population plane (rows padded to 64 nodes) is indexed with 32-bit offsets
+  if (((int64_t)p->nx + 63) / 64 * 64 * p->ny >= (int64_t)1 << 32)
+    return fail(DDFLB_EINVAL, "grid %d x %d: a padded plane reaches 2^32 nodes", p->nx, p->ny);
   if (p->storage < 0 || p->storage > 2) return fail(DDFLB_EINVAL, "storage %d invalid", p->storage);
   for (int k = 0; k < 9; ++k) {
     if (!(p->omega_f[k] >= 0.0 && p->omega_f[k] <= 2.0))

@@ -35,6 +35,8 @@ namespace ddflb {
 
 // per-tile sums of a check: |u|^2, |u - u_prev|^2, rho - rho0, phi^2, (phi - phi_prev)^2
 constexpr int kParts = 5;
+// tile descriptors a CTA keeps in shared memory when its range is this short
+constexpr int kTileCache = 64;
 
 struct BatchInst {
   LbParams P;
@@ -59,9 +61,9 @@ struct BatchStatus {
 };
 
 struct BatchSync {
-  unsigned count;
-  unsigned gen;
-  int err;       // 1: a barrier wait ran out
+  unsigned word;  // barrier counter (see grid_barrier)
+  unsigned pad0;
+  int err;        // 1: a barrier wait ran out (sticky until the batch is reset)
   int pad;
   int64_t step;  // state time of all active instances
   int64_t pad2[5];
@@ -90,38 +92,49 @@ __device__ __forceinline__ unsigned long long now_ns() {
   return t;
 }
 
-// Device-wide barrier for a cooperative grid (all CTAs co-resident).  Returns
-// false if the barrier failed (this or another CTA timed out).
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Device-wide barrier for a cooperative grid (all CTAs co-resident), on one
+// sense-reversing 32-bit counter: CTA 0 adds 2^31 - (N - 1), every other CTA
+// adds 1, so each barrier adds exactly 2^31.  The top bit therefore flips at
+// the last of the N arrivals, whatever their order, and cannot flip back
+// before all N have arrived at the next barrier.  Each CTA makes one acq_rel
+// atomic (releasing its writes) and polls with acquire loads until the top bit
+// differs from the value its atomic returned.  Returns false if the barrier
+// failed: this CTA's wait ran out, or another CTA's did (the sticky error word,
+// read every 32 polls, then stops everyone).
 __device__ bool grid_barrier(BatchSync* s, long long timeout_ns) {
   __syncthreads();
   __shared__ int ok;
   if (threadIdx.x == 0) {
-    volatile unsigned* gen = &s->gen;
-    volatile int* err = &s->err;
-    const unsigned g = *gen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(&s->count, 1u);
-    if (arrived == gridDim.x - 1) {
-      s->count = 0;
-      __threadfence();
-      atomicAdd(&s->gen, 1u);
-    } else {
-      const unsigned long long t0 = now_ns();
-      unsigned spins = 0;
-      while (*gen == g && *err == 0) {
-        __nanosleep(64);
-        if ((++spins & 255u) == 0 && (long long)(now_ns() - t0) > timeout_ns) {
-          atomicExch(&s->err, 1);
+    const unsigned add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
+    unsigned old;
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;"
+                 : "=r"(old)
+                 : "l"(&s->word), "r"(add)
+                 : "memory");
+    const unsigned long long t0 = now_ns();
+    unsigned spins = 0;
+    int good = 1;
+    while (((ld_acquire(&s->word) ^ old) & 0x80000000u) == 0u) {
+      if ((++spins & 31u) == 0u) {
+        if (*(volatile int*)&s->err != 0) {
+          good = 0;
           break;
         }
-        if (spins > (1u << 30)) {  // hard bound independent of the timer
+        // the spin count bounds the wait independently of the timer
+        if ((long long)(now_ns() - t0) > timeout_ns || spins > (1u << 28)) {
           atomicExch(&s->err, 1);
+          good = 0;
           break;
         }
       }
     }
-    __threadfence();
-    ok = (*err == 0);
+    ok = good;
   }
   __syncthreads();
   return ok != 0;
@@ -139,14 +152,14 @@ __device__ __forceinline__ void batch_cell(const LbParams& P, const BatchInst& I
   // a warp whose nodes all have their 8 neighbours inside the lattice pulls
   // without the wall rules (same addresses, so the same values)
   if (BC != BC_PERIODIC && inner)
-    pull<S, BC_PERIODIC>(P, fin, gin, x, y, df, dg);
+    pull<S, BC_PERIODIC, true>(P, fin, gin, x, y, df, dg);
   else
-    pull<S, BC>(P, fin, gin, x, y, df, dg);
+    pull<S, BC, true>(P, fin, gin, x, y, df, dg);
   const Mom mf = moments_flow(df), mg = moments_scalar(dg);
   const Macro q = macro(P, mf, mg);
   relax(P.wf, neq_flow(mf, q), df);
   relax(P.wg, neq_scalar(P, mg, mf, q), dg);
-  const int64_t o = (int64_t)y * P.pitch + x;
+  const uint32_t o = (uint32_t)y * (uint32_t)P.pitch + (uint32_t)x;
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
     Codec<S>::store(fout + a * P.plane + o, df[a], P.sf);
@@ -199,6 +212,13 @@ __global__ void __launch_bounds__(256, 4) k_batch(BatchArgs A) {
   // in shared memory once per instance change, not once per tile
   const int per = (A.ntiles + gridDim.x - 1) / gridDim.x;
   const int tb = blockIdx.x * per, te = min(A.ntiles, tb + per);
+  // a short tile range is read once into shared memory, so a step of small
+  // lattices does not wait on an L2 load of the tile descriptor per tile
+  __shared__ int4 sTiles[kTileCache];
+  const bool cached = te - tb <= kTileCache;
+  if (cached)
+    for (int k = threadIdx.x; k < te - tb; k += blockDim.x) sTiles[k] = A.tiles[tb + k];
+  __syncthreads();
   const int tx = threadIdx.x % A.tile_x, ty = threadIdx.x / A.tile_x;  // place in the tile
   int cur = -1;
   for (int s = 0; s < A.nsteps; ++s) {
@@ -209,7 +229,7 @@ __global__ void __launch_bounds__(256, 4) k_batch(BatchArgs A) {
     const bool snap = A.check_every > 0 && t % A.check_every == 0;
     const bool check_t = snap && t > 0;
     for (int tile = tb; tile < te; ++tile) {
-      const int4 T = A.tiles[tile];
+      const int4 T = cached ? sTiles[tile - tb] : A.tiles[tile];
       if (T.x != cur) {
         __syncthreads();
         const int* srcw = (const int*)(A.inst + T.x);

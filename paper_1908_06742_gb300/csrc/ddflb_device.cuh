@@ -65,22 +65,33 @@ struct DevStatus {
 };
 
 // ------------------------------------------------------------ storage codec
+// Loads take the read-only (non-coherent) path by default, for kernels that run
+// one step per launch; COH = true reads through L2 only (ld.global.cg), for a
+// persistent kernel whose planes are rewritten by other CTAs between its steps.
+template <bool COH, typename T>
+__device__ __forceinline__ T ld_pop(const T* p) {
+  if constexpr (COH) return __ldcg(p);
+  else return __ldg(p);
+}
 template <typename S> struct Codec;
 template <> struct Codec<float> {
-  static __device__ __forceinline__ float load(const float* p, float) { return __ldg(p); }
+  template <bool COH = false>
+  static __device__ __forceinline__ float load(const float* p, float) { return ld_pop<COH>(p); }
   static __device__ __forceinline__ void store(float* p, float v, float) { __stcs(p, v); }
 };
 template <> struct Codec<__half> {
+  template <bool COH = false>
   static __device__ __forceinline__ float load(const __half* p, float inv) {
-    return __half2float(__ldg(p)) * inv;
+    return __half2float(ld_pop<COH>(p)) * inv;
   }
   static __device__ __forceinline__ void store(__half* p, float v, float s) {
     __stcs(reinterpret_cast<unsigned short*>(p), __half_as_ushort(__float2half_rn(v * s)));
   }
 };
 template <> struct Codec<__nv_bfloat16> {
+  template <bool COH = false>
   static __device__ __forceinline__ float load(const __nv_bfloat16* p, float inv) {
-    return __bfloat162float(__ldg(p)) * inv;
+    return __bfloat162float(ld_pop<COH>(p)) * inv;
   }
   static __device__ __forceinline__ void store(__nv_bfloat16* p, float v, float s) {
     __stcs(reinterpret_cast<unsigned short*>(p), __bfloat16_as_ushort(__float2bfloat16_rn(v * s)));
@@ -94,7 +105,7 @@ template <> struct Codec<__nv_bfloat16> {
 // upstream node lies beyond a wall takes the node's own post-collision value of
 // the opposite direction (half-way bounce-back); the flow adds the moving-wall
 // term, the scalar flips sign and adds 2 w (phi_w - phi0).
-template <typename S, int BC>
+template <typename S, int BC, bool COH = false>
 __device__ __forceinline__ void pull(const LbParams& P, const S* __restrict__ fin,
                                      const S* __restrict__ gin, int x, int y, float df[9],
                                      float dg[9]) {
@@ -116,12 +127,17 @@ __device__ __forceinline__ void pull(const LbParams& P, const S* __restrict__ fi
     sym = ym < 0;
     syp = yp >= ny;  // the moving lid
   }
-  const int64_t r0 = (int64_t)y * P.pitch;
-  const int64_t rm = (int64_t)ym * P.pitch;
-  const int64_t rp = (int64_t)yp * P.pitch;
-  const int64_t own = r0 + x;
-  // source offsets of directions 0..8 (source = x - e_a)
-  const int64_t src[9] = {own, r0 + xm, rm + x, r0 + xp, rp + x, rm + xm, rm + xp, rp + xp, rp + xm};
+  // in-plane offsets are 32-bit (a padded plane holds fewer than 2^32
+  // elements); each plane's base pointer is the same for the whole warp
+  const uint32_t pitch = (uint32_t)P.pitch;
+  const uint32_t r0 = (uint32_t)y * pitch;
+  const uint32_t rm = (uint32_t)ym * pitch;
+  const uint32_t rp = (uint32_t)yp * pitch;
+  const uint32_t own = r0 + (uint32_t)x;
+  // source offsets of directions 0..8 (source = x - e_a); an offset whose
+  // source lies beyond a wall is never used
+  const uint32_t src[9] = {own,      r0 + xm, rm + x,  r0 + xp, rp + x,
+                           rm + xm,  rm + xp, rp + xp, rp + xm};
   // direction a's source is beyond a wall
   const bool solid[9] = {false, sxm, sym, sxp, syp, sxm || sym, sxp || sym, sxp || syp, sxm || syp};
   const bool lidl[9] = {false, false, false, false, syp, false, false, syp, syp};
@@ -129,13 +145,14 @@ __device__ __forceinline__ void pull(const LbParams& P, const S* __restrict__ fi
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
     if (BC == BC_PERIODIC) {
-      df[a] = Codec<S>::load(fin + a * pl + src[a], P.isf);
-      dg[a] = Codec<S>::load(gin + a * pl + src[a], P.isg);
+      df[a] = Codec<S>::template load<COH>(fin + a * pl + src[a], P.isf);
+      dg[a] = Codec<S>::template load<COH>(gin + a * pl + src[a], P.isg);
     } else {
       const bool bb = solid[a];
-      const int64_t off = bb ? (int64_t)opp[a] * pl + own : (int64_t)a * pl + src[a];
-      float vf = Codec<S>::load(fin + off, P.isf);
-      float vg = Codec<S>::load(gin + off, P.isg);
+      const int64_t po = (int64_t)(bb ? opp[a] : a) * pl;
+      const uint32_t off = bb ? own : src[a];
+      float vf = Codec<S>::template load<COH>(fin + po + off, P.isf);
+      float vg = Codec<S>::template load<COH>(gin + po + off, P.isg);
       if (bb) {
         const bool lid = lidl[a];
         vf += lid ? P.lid[a] : 0.0f;

@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(256) k_step(LbParams P, const S* __restrict__ 
   else
     pull<S, BC>(P, fin, gin, x, y, df, dg);
   collide<FORCE, SM>(P, x, y, df, dg);
-  const int64_t o = (int64_t)y * P.pitch + x;
+  const uint32_t o = (uint32_t)y * (uint32_t)P.pitch + (uint32_t)x;
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
     Codec<S>::store(fout + a * P.plane + o, df[a], P.sf);
