@@ -39,6 +39,9 @@ def parse():
     ap.add_argument("--n", type=int, default=16384, help="grid side of the Taylor-Green lattice")
     ap.add_argument("--lb-steps", type=int, default=200, help="fused time steps per benchmark step")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--step-path", type=int, default=0, choices=[0, 1, 2],
+                    help="step kernel (ddflb_set_path): 0 default (node pairs for 16-bit "
+                         "storage), 1 one node per thread, 2 node pairs")
     ap.add_argument("--scalar-model", default="mrt", choices=["mrt", "srt", "cascaded", "central"],
                     help="scalar collision (Sec. 3 MRT, App. B SRT, App. C cascaded, App. D central)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -215,6 +218,15 @@ def run_reference(args, world, rank):
 
 
 # ------------------------------------------------------------------ GPU arm
+def step_kernel_name(args):
+    """The step kernel the Taylor-Green context runs for --step-path (the
+    paired kernel takes 16-bit storage, even n and the MRT / SRT scalar)."""
+    pair = args.step_path == 2 or (args.step_path == 0 and args.storage != "fp32")
+    if pair and args.storage != "fp32" and args.n % 2 == 0 and args.scalar_model in ("mrt", "srt"):
+        return "k_step_pair"
+    return "k_step"
+
+
 def traffic_per_launch(args, n_cells):
     """DRAM bytes per k_step launch from the committed ncu summary, if it was
     taken on the current kernel source (else None)."""
@@ -223,8 +235,8 @@ def traffic_per_launch(args, n_cells):
         with open(path) as f:
             d = json.load(f)
         import hashlib
-        e = d.get(f"k_step_{args.storage}" + ("" if args.scalar_model == "mrt" else
-                                               f"_{args.scalar_model}"))
+        e = d.get(f"{step_kernel_name(args)}_{args.storage}" + (
+            "" if args.scalar_model == "mrt" else f"_{args.scalar_model}"))
         if not e:
             return None
         h = hashlib.sha256()
@@ -256,6 +268,8 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.Stream(dev)
     with torch.cuda.stream(stream):
         lat = D.Lattice(cfg, device=dev, stream=stream)
+        if args.step_path:
+            lat.set_path(args.step_path)
         T = inputs.taylor_green(n, 0.01, phi_amp=0.1, xp=torch, device=dev)
         f32 = [a.float() for a in (T.rho, T.ux, T.uy, T.phi, T.grads)]
         del T
@@ -349,7 +363,8 @@ def run_ours(args, world, rank, local):
                    "hbm_pct": round(100 * achieved / peak, 1)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_kind": kind,
-                     "kernel": "k_step", "algorithmic_bytes_per_launch": algo_bytes,
+                     "kernel": step_kernel_name(args),
+                     "algorithmic_bytes_per_launch": algo_bytes,
                      "traffic": traffic_per_launch(args, cells)},
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -182,7 +182,8 @@ struct ddflb_ctx {
   float* stage;
   int64_t step;
   int64_t snap_step;  // step at which uprev was last written (-1: none)
-  int path;           // step kernel: 0 / 1 one node per thread, 2 paired nodes (16-bit storage)
+  int path;           // step kernel: 0 default (paired nodes for 16-bit storage where
+                      // eligible, else one node), 1 one node per thread, 2 paired nodes
   float* stage_out;   // output staging area (host I/O)
   cudaStream_t io_up, io_down;  // streams of host uploads / downloads (null: the context stream)
   cudaEvent_t ev_in_free, ev_in_ready, ev_out_ready, ev_out_free;  // host-I/O ordering
@@ -209,7 +210,9 @@ cudaError_t launch_step_pair(const Launch& L, const void* fin, const void* gin, 
 
 namespace {
 cudaError_t run_step(const ddflb_ctx* c, const void* fin, const void* gin, void* fout, void* gout) {
-  if (c->path == 2 && pair_step_eligible(c->L))
+  // 16-bit storage steps node pairs by default (wider accesses; bit-identical)
+  const bool pair = c->path == 2 || (c->path == 0 && c->L.storage != 0);
+  if (pair && pair_step_eligible(c->L))
     return launch_step_pair(c->L, fin, gin, fout, gout, c->status);
   return launch_step(c->L, fin, gin, fout, gout, c->status);
 }

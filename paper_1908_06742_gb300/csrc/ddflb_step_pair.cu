@@ -3,9 +3,10 @@
 // With FP16/BF16 storage a one-node-per-thread pull moves 2 bytes per memory
 // instruction, so the step is bound by instruction issue rather than by HBM.
 // Here each thread owns the pair of nodes (x0, x0 + 1), x0 even: every plane
-// is read as one aligned 4-byte pair; the populations pulled from x - 1 or
-// x + 1 come from the neighbouring lane's pair by a warp shuffle, with a
-// scalar load only at warp and row edges; stores are 4-byte pairs.  The
+// is read as aligned 4-byte pairs; a plane pulled from x - 1 or x + 1 also
+// reads the aligned pair to the left (x0 - 2) or right (x0 + 2), whose other
+// half the neighbouring thread reads as well (served from L1); stores are
+// 4-byte pairs.  The
 // per-node arithmetic is exactly that of k_step (same device functions), so
 // results are bit-identical to the one-node kernel.
 //
@@ -61,7 +62,6 @@ __global__ void __launch_bounds__(256) k_step_pair(LbParams P, const S* __restri
   constexpr int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
   const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int lane = threadIdx.x & 31;
   if (y >= P.ny) return;  // whole warps share y
   if (status != nullptr && status->diverged) return;
   const int nx = P.nx, ny = P.ny;
@@ -76,14 +76,16 @@ __global__ void __launch_bounds__(256) k_step_pair(LbParams P, const S* __restri
     sym = ym < 0;
     syp = yp >= ny;
   }
-  int xl = x0 - 1, xr = x0 + 2;  // left source of node A, right source of node B
+  // the aligned pairs left and right of the own pair (x0 - 2 holds node A's
+  // source x0 - 1, x0 + 2 node B's source x0 + 2); beyond a wall: none
+  int xl2 = x0 - 2, xr2 = x0 + 2;
   bool sxl = false, sxr = false;
   if (BC == BC_CAVITY) {
-    sxl = xl < 0;
-    sxr = xr >= nx;
+    sxl = xl2 < 0;
+    sxr = xr2 >= nx;
   } else {
-    if (xl < 0) xl += nx;
-    if (xr >= nx) xr -= nx;
+    if (xl2 < 0) xl2 += nx;
+    if (xr2 >= nx) xr2 -= nx;
   }
   const int64_t rows[3] = {(int64_t)ym * P.pitch, (int64_t)y * P.pitch, (int64_t)yp * P.pitch};
   const int64_t own = (int64_t)y * P.pitch + x0;
@@ -101,22 +103,20 @@ __global__ void __launch_bounds__(256) k_step_pair(LbParams P, const S* __restri
     float fa, fb, ga, gb;
     if (ex == 0) {
       fa = Q::lo(fp); fb = Q::hi(fp); ga = Q::lo(gp); gb = Q::hi(gp);
-    } else if (ex == 1) {  // source x - 1: node A from the left lane, node B from own pair
-      float fl = __shfl_up_sync(0xffffffffu, Q::hi(fp), 1);
-      float gl = __shfl_up_sync(0xffffffffu, Q::hi(gp), 1);
-      if ((lane == 0 || x0 == 0) && live && !ysolid && !sxl) {
-        fl = Codec<S>::load(fin + a * pl + ro + xl, 1.0f);
-        gl = Codec<S>::load(gin + a * pl + ro + xl, 1.0f);
+    } else if (ex == 1) {  // source x - 1: node A from the high half of pair x0 - 2
+      typename Q::T fl = Q::zero(), gl = Q::zero();
+      if (live && !ysolid && !sxl) {
+        fl = ld_pair(fin + a * pl + ro + xl2);
+        gl = ld_pair(gin + a * pl + ro + xl2);
       }
-      fa = fl; fb = Q::lo(fp); ga = gl; gb = Q::lo(gp);
-    } else {  // source x + 1: node A from own pair, node B from the right lane
-      float fr = __shfl_down_sync(0xffffffffu, Q::lo(fp), 1);
-      float gr = __shfl_down_sync(0xffffffffu, Q::lo(gp), 1);
-      if ((lane == 31 || x0 + 2 >= nx) && live && !ysolid && !sxr) {
-        fr = Codec<S>::load(fin + a * pl + ro + xr, 1.0f);
-        gr = Codec<S>::load(gin + a * pl + ro + xr, 1.0f);
+      fa = Q::hi(fl); fb = Q::lo(fp); ga = Q::hi(gl); gb = Q::lo(gp);
+    } else {  // source x + 1: node B from the low half of pair x0 + 2
+      typename Q::T fr = Q::zero(), gr = Q::zero();
+      if (live && !ysolid && !sxr) {
+        fr = ld_pair(fin + a * pl + ro + xr2);
+        gr = ld_pair(gin + a * pl + ro + xr2);
       }
-      fa = Q::hi(fp); fb = fr; ga = Q::hi(gp); gb = gr;
+      fa = Q::hi(fp); fb = Q::lo(fr); ga = Q::hi(gp); gb = Q::lo(gr);
     }
     fA[a] = fa * P.isf; fB[a] = fb * P.isf; gA[a] = ga * P.isg; gB[a] = gb * P.isg;
     if (BC != BC_PERIODIC) {

@@ -1,7 +1,8 @@
 """The two step-kernel variants for 16-bit storage (one node per thread, and
-two adjacent nodes per thread with pair accesses and warp shuffles) give
-bit-identical states on every boundary kind and on ragged sizes that end
-mid-warp; odd nx falls back to the one-node kernel."""
+two adjacent nodes per thread with aligned pair accesses) give bit-identical
+states on every boundary kind and on ragged sizes that end mid-warp; odd nx
+falls back to the one-node kernel; the default path for 16-bit storage is the
+paired kernel."""
 import numpy as np
 import pytest
 
@@ -37,6 +38,23 @@ def test_pair_kernel_bit_identical(storage, bc, shape):
         lat.init(F.rho, F.ux, F.uy, F.phi, F.grads).step(7)
         out.append(lat.populations())   # every node (the raw buffer's row padding is never written)
     assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+def test_default_path_for_16bit_storage_is_the_pair_kernel(storage):
+    """Path 0 (default) steps 16-bit lattices with the paired kernel: same
+    state as path 2 and as path 1, on a lattice with an odd-width wrap."""
+    nx, ny = 130, 41
+    s = spec(nx, ny, nu=0.05, D_phi=0.02, storage=storage,
+             scale=2.0 ** 10 if storage == "fp16" else 0.0)
+    F = inputs.random_state(nx, ny, seed=17)
+    out = []
+    for path in (0, 1, 2):
+        lat = D.Lattice(gpu_config(s)).set_path(path)
+        lat.init(F.rho, F.ux, F.uy, F.phi, F.grads).step(9)
+        out.append(lat.populations())
+    for k in (1, 2):
+        assert torch.equal(out[0][0], out[k][0]) and torch.equal(out[0][1], out[k][1])
 
 
 def test_pair_kernel_matches_oracle_emulation_scale():
