@@ -39,9 +39,9 @@ def parse():
     ap.add_argument("--n", type=int, default=16384, help="grid side of the Taylor-Green lattice")
     ap.add_argument("--lb-steps", type=int, default=200, help="fused time steps per benchmark step")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
-    ap.add_argument("--step-path", type=int, default=0, choices=[0, 1, 2],
-                    help="step kernel (ddflb_set_path): 0 default (node pairs for 16-bit "
-                         "storage), 1 one node per thread, 2 node pairs")
+    ap.add_argument("--step-path", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="step kernel (ddflb_set_path): 0 default (groups of 4 nodes for "
+                         "16-bit storage), 1 one node per thread, 2 node pairs, 3 groups of 4")
     ap.add_argument("--scalar-model", default="mrt", choices=["mrt", "srt", "cascaded", "central"],
                     help="scalar collision (Sec. 3 MRT, App. B SRT, App. C cascaded, App. D central)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -221,7 +221,10 @@ def run_reference(args, world, rank):
 def step_kernel_name(args):
     """The step kernel the Taylor-Green context runs for --step-path (the
     paired kernel takes 16-bit storage, even n and the MRT / SRT scalar)."""
-    pair = args.step_path == 2 or (args.step_path == 0 and args.storage != "fp32")
+    if (args.step_path in (0, 3) and args.storage != "fp32" and args.n % 4 == 0
+            and args.scalar_model in ("mrt", "srt")):
+        return "k_step_quad"
+    pair = args.step_path in (2, 3) or (args.step_path == 0 and args.storage != "fp32")
     if pair and args.storage != "fp32" and args.n % 2 == 0 and args.scalar_model in ("mrt", "srt"):
         return "k_step_pair"
     return "k_step"

@@ -271,8 +271,9 @@ ddflb_status ddflb_reduce_noalloc(const ddflb_params* p, const void* dev_state,
 /* Autotuner for the step kernel: times each thread-block shape (128x1, 256x1,
  * 64x2, 32x4, 64x4, 32x8, 64x1) with each kernel variant (path 1: one node per
  * thread; path 2, 16-bit storage with even nx only: two adjacent nodes per
- * thread with aligned 4-byte pair accesses) over trial_steps with CUDA events and keeps
- * the fastest.  Runs on zeroed populations, so it OVERWRITES the state and
+ * thread with aligned 4-byte pair accesses), and path 3 (four nodes per
+ * thread, its own 128x1 block) once where it applies, over trial_steps with
+ * CUDA events, and keeps the fastest.  Runs on zeroed populations, so it OVERWRITES the state and
  * resets the step counter: call it before ddflb_init.  Synchronises. */
 ddflb_status ddflb_autotune(ddflb_ctx* c, int32_t trial_steps, int32_t* block_x,
                             int32_t* block_y, int32_t* path, double* ms_per_step);
@@ -282,8 +283,10 @@ ddflb_status ddflb_set_block(ddflb_ctx* c, int32_t block_x, int32_t block_y);
 /* Step kernel variant: 1 one node per thread; 2 paired nodes, two adjacent
  * nodes per thread with aligned 4-byte pair accesses (16-bit storage, even nx,
  * unforced, MRT or SRT scalar; otherwise falls back to one node per thread);
- * 0 (default) = 2 for 16-bit storage, 1 for FP32.  All give bit-identical
- * results; which is faster depends on the shape, so the autotuner times both. */
+ * 3 four adjacent nodes per thread with aligned 8-byte accesses (as 2, and
+ * periodic with nx a multiple of 4; otherwise falls back to 2, then 1);
+ * 0 (default) = 3 for 16-bit storage, 1 for FP32.  All give bit-identical
+ * results; which is faster depends on the shape, so the autotuner times them. */
 ddflb_status ddflb_set_path(ddflb_ctx* c, int32_t path);
 
 /* Spatially varying part of the body force (Sec. 2; e.g. the four-rolls mill

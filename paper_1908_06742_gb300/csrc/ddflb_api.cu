@@ -182,8 +182,9 @@ struct ddflb_ctx {
   float* stage;
   int64_t step;
   int64_t snap_step;  // step at which uprev was last written (-1: none)
-  int path;           // step kernel: 0 default (paired nodes for 16-bit storage where
-                      // eligible, else one node), 1 one node per thread, 2 paired nodes
+  int path;           // step kernel: 0 default (16-bit storage: groups of 4 nodes, else
+                      // pairs, where eligible; else one node), 1 one node per thread,
+                      // 2 paired nodes, 3 groups of 4 nodes (periodic)
   float* stage_out;   // output staging area (host I/O)
   cudaStream_t io_up, io_down;  // streams of host uploads / downloads (null: the context stream)
   cudaEvent_t ev_in_free, ev_in_ready, ev_out_ready, ev_out_free;  // host-I/O ordering
@@ -206,12 +207,18 @@ namespace ddflb {
 bool pair_step_eligible(const Launch& L);
 cudaError_t launch_step_pair(const Launch& L, const void* fin, const void* gin, void* fout,
                              void* gout, const DevStatus* st);
+// periodic 16-bit lattices with nx a multiple of 4: four nodes per thread
+bool quad_step_eligible(const Launch& L);
+cudaError_t launch_step_quad(const Launch& L, const void* fin, const void* gin, void* fout,
+                             void* gout, const DevStatus* st);
 }  // namespace ddflb
 
 namespace {
 cudaError_t run_step(const ddflb_ctx* c, const void* fin, const void* gin, void* fout, void* gout) {
-  // 16-bit storage steps node pairs by default (wider accesses; bit-identical)
-  const bool pair = c->path == 2 || (c->path == 0 && c->L.storage != 0);
+  // 16-bit storage steps node groups by default (wider accesses; bit-identical)
+  if ((c->path == 3 || c->path == 0) && quad_step_eligible(c->L))
+    return launch_step_quad(c->L, fin, gin, fout, gout, c->status);
+  const bool pair = c->path == 2 || c->path == 3 || (c->path == 0 && c->L.storage != 0);
   if (pair && pair_step_eligible(c->L))
     return launch_step_pair(c->L, fin, gin, fout, gout, c->status);
   return launch_step(c->L, fin, gin, fout, gout, c->status);
@@ -551,11 +558,13 @@ ddflb_status ddflb_autotune(ddflb_ctx* c, int32_t trial_steps, int32_t* block_x,
   int bestp = 1;
   const int saved_path = c->path;
   const size_t gofs = 9 * (size_t)c->lay.pitch * c->p.ny * elem_size(c->p.storage);
-  for (int pth = 1; pth <= 2 && e == cudaSuccess; ++pth) {
+  for (int pth = 1; pth <= 3 && e == cudaSuccess; ++pth) {
     for (const auto& sh : shapes) {
       c->L.block = dim3(sh[0], sh[1], 1);
       c->path = pth;
       if (pth == 2 && !pair_step_eligible(c->L)) continue;
+      // the 4-node kernel has its own 128 x 1 block: timed once
+      if (pth == 3 && (!quad_step_eligible(c->L) || &sh != &shapes[0])) continue;
       for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
         if (rep == 1) e = cudaEventRecord(e0, s);
         for (int i = 0; i < trial_steps && e == cudaSuccess; ++i) {
@@ -598,7 +607,7 @@ ddflb_status ddflb_autotune(ddflb_ctx* c, int32_t trial_steps, int32_t* block_x,
 }
 
 ddflb_status ddflb_set_path(ddflb_ctx* c, int32_t path) {
-  if (!c || path < 0 || path > 2) return fail(DDFLB_EINVAL, "path must be 0, 1 or 2");
+  if (!c || path < 0 || path > 3) return fail(DDFLB_EINVAL, "path must be 0, 1, 2 or 3");
   c->path = path;
   return DDFLB_OK;
 }

@@ -161,6 +161,105 @@ __global__ void __launch_bounds__(256) k_step_pair(LbParams P, const S* __restri
   }
 }
 
+// Four adjacent nodes per thread (x0 .. x0 + 3, x0 a multiple of 4) on a
+// periodic lattice with nx a multiple of 4: every plane is read as one aligned
+// 8-byte group; a plane pulled from x - 1 (x + 1) also reads the group to the
+// left (right), of which node x0 (x0 + 3) takes the last (first) element.  The
+// four nodes are collided one after another with k_step's device functions and
+// stored as 8-byte groups: bit-identical to the one-node kernel.
+template <typename S>
+__device__ __forceinline__ uint2 ld_quad(const S* p) {
+  return __ldg(reinterpret_cast<const uint2*>(p));
+}
+template <typename S> __device__ __forceinline__ float half_of(unsigned w, int hi);
+template <> __device__ __forceinline__ float half_of<__half>(unsigned w, int hi) {
+  return __half2float(__ushort_as_half((unsigned short)(hi ? w >> 16 : w & 0xffffu)));
+}
+template <> __device__ __forceinline__ float half_of<__nv_bfloat16>(unsigned w, int hi) {
+  return __bfloat162float(__ushort_as_bfloat16((unsigned short)(hi ? w >> 16 : w & 0xffffu)));
+}
+// element k (0..3) of an 8-byte group
+template <typename S> __device__ __forceinline__ float elem(uint2 v, int k) {
+  return half_of<S>(k < 2 ? v.x : v.y, k & 1);
+}
+template <typename S> __device__ __forceinline__ unsigned bits_of(float v, float s);
+template <> __device__ __forceinline__ unsigned bits_of<__half>(float v, float s) {
+  return __half_as_ushort(__float2half_rn(v * s));
+}
+template <> __device__ __forceinline__ unsigned bits_of<__nv_bfloat16>(float v, float s) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn(v * s));
+}
+
+template <typename S>
+__global__ void __launch_bounds__(128) k_step_quad(LbParams P, const S* __restrict__ fin,
+                                                   const S* __restrict__ gin,
+                                                   S* __restrict__ fout, S* __restrict__ gout,
+                                                   const DevStatus* __restrict__ status) {
+  constexpr int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+  constexpr int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+  const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x0 >= P.nx || y >= P.ny) return;
+  if (status != nullptr && status->diverged) return;
+  const int nx = P.nx, ny = P.ny;
+  const int64_t pl = P.plane;
+  const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+  const int xl = x0 == 0 ? nx - 4 : x0 - 4, xr = x0 + 4 == nx ? 0 : x0 + 4;
+  const int64_t rows[3] = {(int64_t)ym * P.pitch, (int64_t)y * P.pitch, (int64_t)yp * P.pitch};
+  // own groups of the 18 planes, and the one element node x0 (x0 + 3) takes
+  // from the left (right) group of the x-shifted planes
+  uint2 fo[9], go[9];
+  float fe[9], ge[9];
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    const int64_t ro = rows[1 - EY[a]];
+    fo[a] = ld_quad(fin + a * pl + ro + x0);
+    go[a] = ld_quad(gin + a * pl + ro + x0);
+    if (EX[a] == 1) {
+      fe[a] = elem<S>(ld_quad(fin + a * pl + ro + xl), 3);
+      ge[a] = elem<S>(ld_quad(gin + a * pl + ro + xl), 3);
+    } else if (EX[a] == -1) {
+      fe[a] = elem<S>(ld_quad(fin + a * pl + ro + xr), 0);
+      ge[a] = elem<S>(ld_quad(gin + a * pl + ro + xr), 0);
+    } else {
+      fe[a] = ge[a] = 0.0f;
+    }
+  }
+  unsigned fw[9][2], gw[9][2];  // packed results: [plane][low / high word]
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    float df[9], dg[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      // node x0 + k pulls element k - e_ax of the own group (or the neighbour's)
+      const int e = k - EX[a];
+      df[a] = (e < 0 || e > 3 ? fe[a] : elem<S>(fo[a], e)) * P.isf;
+      dg[a] = (e < 0 || e > 3 ? ge[a] : elem<S>(go[a], e)) * P.isg;
+    }
+    const Mom mf = moments_flow(df), mg = moments_scalar(dg);
+    const Macro q = macro(P, mf, mg);
+    relax(P.wf, neq_flow(mf, q), df);
+    relax(P.wg, neq_scalar(P, mg, mf, q), dg);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      const unsigned bf = bits_of<S>(df[a], P.sf), bg = bits_of<S>(dg[a], P.sg);
+      if (k & 1) {
+        fw[a][k >> 1] |= bf << 16;
+        gw[a][k >> 1] |= bg << 16;
+      } else {
+        fw[a][k >> 1] = bf;
+        gw[a][k >> 1] = bg;
+      }
+    }
+  }
+  const int64_t own = (int64_t)y * P.pitch + x0;
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    __stcs(reinterpret_cast<uint2*>(fout + a * pl + own), make_uint2(fw[a][0], fw[a][1]));
+    __stcs(reinterpret_cast<uint2*>(gout + a * pl + own), make_uint2(gw[a][0], gw[a][1]));
+  }
+}
+
 namespace {
 template <typename S, int BC>
 cudaError_t go(const Launch& L, const void* fin, const void* gin, void* fout, void* gout,
@@ -181,6 +280,25 @@ cudaError_t go_bc(const Launch& L, const void* fin, const void* gin, void* fout,
   }
 }
 }  // namespace
+
+bool quad_step_eligible(const Launch& L) {
+  return !L.force && L.P.smodel < 2 && L.storage != 0 && L.P_bc == BC_PERIODIC &&
+         L.P.nx % 4 == 0;
+}
+
+cudaError_t launch_step_quad(const Launch& L, const void* fin, const void* gin, void* fout,
+                             void* gout, const DevStatus* st) {
+  const dim3 b(128, 1);
+  const dim3 g((L.P.nx / 4 + b.x - 1) / b.x, L.P.ny);
+  if (L.storage == 1)
+    k_step_quad<__half><<<g, b, 0, L.stream>>>(L.P, (const __half*)fin, (const __half*)gin,
+                                               (__half*)fout, (__half*)gout, st);
+  else
+    k_step_quad<__nv_bfloat16><<<g, b, 0, L.stream>>>(
+        L.P, (const __nv_bfloat16*)fin, (const __nv_bfloat16*)gin, (__nv_bfloat16*)fout,
+        (__nv_bfloat16*)gout, st);
+  return cudaGetLastError();
+}
 
 bool pair_step_eligible(const Launch& L) {
   return !L.force && L.P.smodel < 2 && L.storage != 0 && L.P.nx % 2 == 0 &&

@@ -41,6 +41,25 @@ def test_pair_kernel_bit_identical(storage, bc, shape):
 
 
 @pytest.mark.parametrize("storage", ["fp16", "bf16"])
+@pytest.mark.parametrize("shape,bc", [((200, 77), "periodic"), ((132, 66), "periodic"),
+                                      ((4, 5), "periodic"), ((1024, 33), "periodic"),
+                                      ((130, 40), "periodic"), ((200, 50), "cavity")])
+def test_quad_kernel_bit_identical(storage, shape, bc):
+    """Path 3 (four nodes per thread, periodic, nx a multiple of 4; otherwise
+    the paired or one-node kernel) against path 1, 7 steps."""
+    nx, ny = shape
+    s = spec(nx, ny, bc=bc, nu=0.05, D_phi=0.02, u_lid=0.05, phi_lid=1.3, phi_wall=0.7,
+             storage=storage, scale=2.0 ** 10 if storage == "fp16" else 0.0)
+    F = inputs.random_state(nx, ny, seed=nx * 7 + ny)
+    out = []
+    for path in (1, 3):
+        lat = D.Lattice(gpu_config(s)).set_path(path)
+        lat.init(F.rho, F.ux, F.uy, F.phi, F.grads).step(7)
+        out.append(lat.populations())
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
 def test_default_path_for_16bit_storage_is_the_pair_kernel(storage):
     """Path 0 (default) steps 16-bit lattices with the paired kernel: same
     state as path 2 and as path 1, on a lattice with an odd-width wrap."""
