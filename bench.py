@@ -362,7 +362,7 @@ def run_ours(args, world, rank, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload_name(args), "grid": n, "lb_steps_per_step": lb,
                    "storage": args.storage, "parallelism": "replicas" if world > 1 else "single",
-                   "l2": f"inputs larger than L2 ({2 * algo_bytes / 2 / 1e9:.1f} GB of populations per copy)",
+                   "l2": f"inputs larger than L2 ({algo_bytes / 2 / 1e9:.1f} GB of populations per buffer)",
                    "hbm_pct": round(100 * achieved / peak, 1)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_kind": kind,
