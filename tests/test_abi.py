@@ -68,6 +68,24 @@ def test_invalid_parameters(lib, field, value, msg):
     assert msg in lib.ddflb_last_error().decode()
 
 
+def test_grid_size_limit(lib):
+    """Population planes are indexed with 32-bit offsets: a padded plane (rows
+    rounded up to 64 nodes) must hold fewer than 2^32 elements.  Checked
+    without allocating: the workspace query validates the parameters."""
+    c = good(); c.nx, c.ny = 65536, 65536          # exactly 2^32 nodes
+    p = c.to_c()
+    assert lib.ddflb_workspace_bytes(ctypes.byref(p)) == 0
+    assert "2^32" in lib.ddflb_last_error().decode()
+    c = good(); c.nx, c.ny = 65537, 65535          # pads to 65600 x 65535 > 2^32
+    p = c.to_c()
+    assert lib.ddflb_workspace_bytes(ctypes.byref(p)) == 0
+    c = good(); c.nx, c.ny = 65536, 65535          # the largest square-ish plane that fits
+    c.storage = "fp16"
+    p = c.to_c()
+    n = lib.ddflb_workspace_bytes(ctypes.byref(p))
+    assert n >= 2 * 18 * 65536 * 65535 * 2
+
+
 def test_conserved_rates_must_be_zero(lib):
     c = good(); c.omega_f = (0, 0.5, 0, 1.2, 1.5, 1.5, 1, 1, 1)
     p = c.to_c()
