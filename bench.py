@@ -224,6 +224,8 @@ def step_kernel_name(args):
     if (args.step_path in (0, 3) and args.storage != "fp32" and args.n % 4 == 0
             and args.scalar_model in ("mrt", "srt")):
         return "k_step_quad"
+    # the Taylor-Green lattice is periodic: there the default takes pairs when
+    # n is not a multiple of 4
     pair = args.step_path in (2, 3) or (args.step_path == 0 and args.storage != "fp32")
     if pair and args.storage != "fp32" and args.n % 2 == 0 and args.scalar_model in ("mrt", "srt"):
         return "k_step_pair"

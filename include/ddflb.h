@@ -283,9 +283,11 @@ ddflb_status ddflb_set_block(ddflb_ctx* c, int32_t block_x, int32_t block_y);
 /* Step kernel variant: 1 one node per thread; 2 paired nodes, two adjacent
  * nodes per thread with aligned 4-byte pair accesses (16-bit storage, even nx,
  * unforced, MRT or SRT scalar; otherwise falls back to one node per thread);
- * 3 four adjacent nodes per thread with aligned 8-byte accesses (as 2, and
- * periodic with nx a multiple of 4; otherwise falls back to 2, then 1);
- * 0 (default) = 3 for 16-bit storage, 1 for FP32.  All give bit-identical
+ * 3 four adjacent nodes per thread with aligned 8-byte accesses (as 2, with
+ * nx a multiple of 4; nodes next to a wall one by one; otherwise falls back to
+ * 2, then 1);
+ * 0 (default) = 3 for 16-bit storage (else 2 on a periodic lattice, else 1),
+ * 1 for FP32.  All give bit-identical
  * results; which is faster depends on the shape, so the autotuner times them. */
 ddflb_status ddflb_set_path(ddflb_ctx* c, int32_t path);
 

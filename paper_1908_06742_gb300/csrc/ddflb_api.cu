@@ -183,8 +183,8 @@ struct ddflb_ctx {
   int64_t step;
   int64_t snap_step;  // step at which uprev was last written (-1: none)
   int path;           // step kernel: 0 default (16-bit storage: groups of 4 nodes, else
-                      // pairs, where eligible; else one node), 1 one node per thread,
-                      // 2 paired nodes, 3 groups of 4 nodes (periodic)
+                      // pairs on a periodic lattice, where eligible; else one node),
+                      // 1 one node per thread, 2 paired nodes, 3 groups of 4 nodes
   float* stage_out;   // output staging area (host I/O)
   cudaStream_t io_up, io_down;  // streams of host uploads / downloads (null: the context stream)
   cudaEvent_t ev_in_free, ev_in_ready, ev_out_ready, ev_out_free;  // host-I/O ordering
@@ -218,7 +218,9 @@ cudaError_t run_step(const ddflb_ctx* c, const void* fin, const void* gin, void*
   // 16-bit storage steps node groups by default (wider accesses; bit-identical)
   if ((c->path == 3 || c->path == 0) && quad_step_eligible(c->L))
     return launch_step_quad(c->L, fin, gin, fout, gout, c->status);
-  const bool pair = c->path == 2 || c->path == 3 || (c->path == 0 && c->L.storage != 0);
+  // (with walls the paired kernel is no faster than one node per thread)
+  const bool pair = c->path == 2 || c->path == 3 ||
+                    (c->path == 0 && c->L.storage != 0 && c->L.P_bc == BC_PERIODIC);
   if (pair && pair_step_eligible(c->L))
     return launch_step_pair(c->L, fin, gin, fout, gout, c->status);
   return launch_step(c->L, fin, gin, fout, gout, c->status);

@@ -162,11 +162,14 @@ __global__ void __launch_bounds__(256) k_step_pair(LbParams P, const S* __restri
 }
 
 // Four adjacent nodes per thread (x0 .. x0 + 3, x0 a multiple of 4) on a
-// periodic lattice with nx a multiple of 4: every plane is read as one aligned
-// 8-byte group; a plane pulled from x - 1 (x + 1) also reads the group to the
-// left (right), of which node x0 (x0 + 3) takes the last (first) element.  The
-// four nodes are collided one after another with k_step's device functions and
-// stored as 8-byte groups: bit-identical to the one-node kernel.
+// lattice with nx a multiple of 4: every plane is read as one aligned 8-byte
+// group; a plane pulled from x - 1 (x + 1) also reads the group to the left
+// (right), of which node x0 (x0 + 3) takes the last (first) element.  The four
+// nodes are collided one after another with k_step's device functions and
+// stored as 8-byte groups.  A group with a node next to a wall (rows 0 and
+// ny - 1; for the cavity also the first and last group of a row) steps its
+// nodes one by one with k_step's pull and wall rules instead.  Bit-identical to
+// the one-node kernel.
 template <typename S>
 __device__ __forceinline__ uint2 ld_quad(const S* p) {
   return __ldg(reinterpret_cast<const uint2*>(p));
@@ -190,7 +193,7 @@ template <> __device__ __forceinline__ unsigned bits_of<__nv_bfloat16>(float v, 
   return __bfloat16_as_ushort(__float2bfloat16_rn(v * s));
 }
 
-template <typename S>
+template <typename S, int BC>
 __global__ void __launch_bounds__(128) k_step_quad(LbParams P, const S* __restrict__ fin,
                                                    const S* __restrict__ gin,
                                                    S* __restrict__ fout, S* __restrict__ gout,
@@ -203,6 +206,25 @@ __global__ void __launch_bounds__(128) k_step_quad(LbParams P, const S* __restri
   if (status != nullptr && status->diverged) return;
   const int nx = P.nx, ny = P.ny;
   const int64_t pl = P.plane;
+  if (BC != BC_PERIODIC &&
+      (y == 0 || y == ny - 1 || (BC == BC_CAVITY && (x0 == 0 || x0 + 4 == nx)))) {
+    // next to a wall: node by node, as k_step
+    const uint32_t o0 = (uint32_t)y * (uint32_t)P.pitch + (uint32_t)x0;
+#pragma unroll 1
+    for (int k = 0; k < 4; ++k) {
+      float df[9], dg[9];
+      pull<S, BC>(P, fin, gin, x0 + k, y, df, dg);
+      collide<false, 0>(P, x0 + k, y, df, dg);
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        Codec<S>::store(fout + a * pl + (o0 + k), df[a], P.sf);
+        Codec<S>::store(gout + a * pl + (o0 + k), dg[a], P.sg);
+      }
+    }
+    return;
+  }
+  // (with walls this group is away from them: no row wraps, and for the cavity
+  // no column wraps either)
   const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
   const int xl = x0 == 0 ? nx - 4 : x0 - 4, xr = x0 + 4 == nx ? 0 : x0 + 4;
   const int64_t rows[3] = {(int64_t)ym * P.pitch, (int64_t)y * P.pitch, (int64_t)yp * P.pitch};
@@ -282,22 +304,34 @@ cudaError_t go_bc(const Launch& L, const void* fin, const void* gin, void* fout,
 }  // namespace
 
 bool quad_step_eligible(const Launch& L) {
-  return !L.force && L.P.smodel < 2 && L.storage != 0 && L.P_bc == BC_PERIODIC &&
-         L.P.nx % 4 == 0;
+  return !L.force && L.P.smodel < 2 && L.storage != 0 && L.P.nx % 4 == 0;
 }
+
+namespace {
+template <typename S, int BC>
+cudaError_t go_quad(const Launch& L, const void* fin, const void* gin, void* fout, void* gout,
+                    const DevStatus* st) {
+  const dim3 b(128, 1);
+  const dim3 g((L.P.nx / 4 + b.x - 1) / b.x, L.P.ny);
+  k_step_quad<S, BC><<<g, b, 0, L.stream>>>(L.P, (const S*)fin, (const S*)gin, (S*)fout,
+                                            (S*)gout, st);
+  return cudaGetLastError();
+}
+template <typename S>
+cudaError_t go_quad_bc(const Launch& L, const void* fin, const void* gin, void* fout,
+                       void* gout, const DevStatus* st) {
+  switch (L.P_bc) {
+    case BC_PERIODIC: return go_quad<S, BC_PERIODIC>(L, fin, gin, fout, gout, st);
+    case BC_CAVITY: return go_quad<S, BC_CAVITY>(L, fin, gin, fout, gout, st);
+    default: return go_quad<S, BC_CHANNEL>(L, fin, gin, fout, gout, st);
+  }
+}
+}  // namespace
 
 cudaError_t launch_step_quad(const Launch& L, const void* fin, const void* gin, void* fout,
                              void* gout, const DevStatus* st) {
-  const dim3 b(128, 1);
-  const dim3 g((L.P.nx / 4 + b.x - 1) / b.x, L.P.ny);
-  if (L.storage == 1)
-    k_step_quad<__half><<<g, b, 0, L.stream>>>(L.P, (const __half*)fin, (const __half*)gin,
-                                               (__half*)fout, (__half*)gout, st);
-  else
-    k_step_quad<__nv_bfloat16><<<g, b, 0, L.stream>>>(
-        L.P, (const __nv_bfloat16*)fin, (const __nv_bfloat16*)gin, (__nv_bfloat16*)fout,
-        (__nv_bfloat16*)gout, st);
-  return cudaGetLastError();
+  if (L.storage == 1) return go_quad_bc<__half>(L, fin, gin, fout, gout, st);
+  return go_quad_bc<__nv_bfloat16>(L, fin, gin, fout, gout, st);
 }
 
 bool pair_step_eligible(const Launch& L) {

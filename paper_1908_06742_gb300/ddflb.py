@@ -373,9 +373,10 @@ class Lattice:
         return self
 
     def set_path(self, path: int):
-        """Step kernel variant: 0 automatic (16-bit storage: groups of 4 or pairs
-        where they apply), 1 one node per thread, 2 paired nodes, 3 groups of 4
-        nodes (periodic, nx a multiple of 4).  All give the same state."""
+        """Step kernel variant: 0 automatic (16-bit storage: groups of 4 nodes
+        where nx is a multiple of 4, else pairs on periodic lattices), 1 one node
+        per thread, 2 paired nodes, 3 groups of 4 nodes.  All give the same
+        state."""
         _check(self.lib.ddflb_set_path(self._h, int(path)))
         return self
 

@@ -43,10 +43,13 @@ def test_pair_kernel_bit_identical(storage, bc, shape):
 @pytest.mark.parametrize("storage", ["fp16", "bf16"])
 @pytest.mark.parametrize("shape,bc", [((200, 77), "periodic"), ((132, 66), "periodic"),
                                       ((4, 5), "periodic"), ((1024, 33), "periodic"),
-                                      ((130, 40), "periodic"), ((200, 50), "cavity")])
+                                      ((130, 40), "periodic"), ((200, 50), "cavity"),
+                                      ((256, 37), "cavity"), ((4, 3), "cavity"), ((8, 2), "cavity"),
+                                      ((132, 66), "channel"), ((8, 2), "channel"),
+                                      ((130, 9), "channel")])
 def test_quad_kernel_bit_identical(storage, shape, bc):
-    """Path 3 (four nodes per thread, periodic, nx a multiple of 4; otherwise
-    the paired or one-node kernel) against path 1, 7 steps."""
+    """Path 3 (four nodes per thread, nx a multiple of 4, node by node next to
+    walls; otherwise the paired or one-node kernel) against path 1, 7 steps."""
     nx, ny = shape
     s = spec(nx, ny, bc=bc, nu=0.05, D_phi=0.02, u_lid=0.05, phi_lid=1.3, phi_wall=0.7,
              storage=storage, scale=2.0 ** 10 if storage == "fp16" else 0.0)
