@@ -47,8 +47,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="tg",
-                    choices=["tg", "batch", "cavity", "surrogate", "gemm"],
-                    help="tg: Taylor-Green throughput sweep point; batch: 512 uneven cavities; "
+                    choices=["tg", "sweep", "batch", "cavity", "surrogate", "gemm"],
+                    help="tg: Taylor-Green throughput point; sweep: Taylor-Green at N = 1024, "
+                         "4096, 8192, 16384 for each storage; batch: 512 uneven cavities; "
                          "cavity: 256^2 cavities run to steady state")
     ap.add_argument("--instances", type=int, default=512)
     ap.add_argument("--gemm-shape", default=None,
@@ -595,6 +596,69 @@ GEMM_SHAPES = [(262144, 32, 144, 1), (65536, 64, 288, 1), (16384, 128, 576, 1),
                (128, 1152, 65536, 16)]
 
 
+def run_sweep(args, world, rank, local):
+    """Throughput sweep: decaying Taylor-Green (U0 = 0.01, nu = D = 0.01) on N x N
+    lattices, N = 1024, 4096, 8192, 16384, FP32 / FP16 / BF16 storage (default
+    step kernel of each), --lb-steps fused steps timed with CUDA events after
+    as many untimed ones.  A row whose two population buffers fit in the 129 MB
+    L2 is marked l2_resident (its GB/s are not HBM figures)."""
+    import torch
+    from paper_1908_06742_gb300 import build as B
+    from paper_1908_06742_gb300 import ddflb as D
+    from paper_1908_06742_gb300 import inputs
+
+    B.build()
+    D.load()
+    dev = torch.device("cuda", local)
+    peak, kind = peaks()
+    wf, wg = rates(0.01)
+    rows = []
+    stream = torch.cuda.Stream(dev)
+    for st in ("fp32", "fp16", "bf16"):
+        for n in (1024, 4096, 8192, 16384):
+            a = argparse.Namespace(**vars(args))
+            a.n, a.storage, a.step_path = n, st, 0
+            cfg = D.Config(nx=n, ny=n, storage=st, omega_f=wf, omega_g=wg,
+                           scale_f=2.0 ** 10 if st == "fp16" else 0.0,
+                           scale_g=2.0 ** 10 if st == "fp16" else 0.0)
+            with torch.cuda.stream(stream):
+                lat = D.Lattice(cfg, device=dev, stream=stream)
+                T = inputs.taylor_green(n, 0.01, phi_amp=0.1, xp=torch, device=dev)
+                lat.init(*[t.float() for t in (T.rho, T.ux, T.uy, T.phi, T.grads)])
+                del T
+                lb = args.lb_steps
+                lat.step(lb)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                barrier(world)
+                torch.cuda.synchronize(dev)
+                e0.record(stream)
+                lat.step(lb)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                ms = max_over_ranks(world, e0.elapsed_time(e1))
+                diverged = lat.stats()["diverged"]
+                del lat
+            torch.cuda.empty_cache()
+            bpc = BYTES_PER_CELL[st]
+            gbs = bpc * n * n * lb / (ms / 1e3) / 1e9
+            rows.append({"n": n, "storage": st, "kernel": step_kernel_name(a),
+                         "mlups": round(world * n * n * lb / (ms / 1e3) / 1e6, 1),
+                         "gbs": round(gbs, 1), "frac": round(gbs / peak, 4),
+                         "l2_resident": bpc * n * n < 129e6, "diverged": bool(diverged)})
+    if rank != 0:
+        return
+    top = [r for r in rows if r["n"] == 16384 and r["storage"] == "fp32"][0]
+    print(json.dumps({
+        "metric": METRIC, "value": top["mlups"], "unit": "MLUPS", "n_gpus": world,
+        "steps": 1, "warmup": 1, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"taylor-green throughput sweep, N = 1024..16384, fp32/fp16/bf16, "
+                               f"{args.lb_steps} timed fused steps each; value = fp32 at 16384^2"},
+        "roofline": {"bound": "hbm", "achieved": top["gbs"], "peak": peak, "unit": "GB/s",
+                     "frac": top["frac"], "peak_kind": kind, "kernel": top["kernel"]},
+        "rows": rows}))
+
+
 def run_gemm(args, world, rank, local):
     """BF16 GEMM throughput of the surrogate's contraction shapes on the
     tensor-core paths (0: tcgen05 + TMA, persistent; 1: mma.sync; 2: tcgen05,
@@ -679,6 +743,8 @@ def main():
         run_surrogate(args, world, rank, local)
     elif args.workload == "gemm":
         run_gemm(args, world, rank, local)
+    elif args.workload == "sweep":
+        run_sweep(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

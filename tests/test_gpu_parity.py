@@ -267,6 +267,57 @@ def test_16bit_storage_taylor_green(storage, scale):
         assert e["u"] < 2e-3 and e["phi"] < 2e-3
 
 
+# --------------------------------------------------------------- throughput-sweep accuracy
+SWEEP_REF = {}
+
+
+def sweep_errors(fg, fo):
+    """Relative-L2 errors: u (both components), phi, S (worst component over
+    the RMS of the largest) and omega."""
+    e = {"u": rel_l2(np.stack([fg["ux"], fg["uy"]]), np.stack([fo["ux"], fo["uy"]])),
+         "phi": rel_l2(fg["phi"], fo["phi"]), "omega": rel_l2(fg["omega"], fo["omega"])}
+    ref = math.sqrt(max(np.mean(fo[k] ** 2) for k in ("sxx", "sxy", "syy")))
+    e["S"] = max(math.sqrt(np.mean((fg[k] - fo[k]) ** 2)) for k in ("sxx", "sxy", "syy")) / ref
+    return e
+
+
+@pytest.mark.parametrize("storage,scale", [("fp32", 0.0), ("fp16", 2.0 ** 10), ("bf16", 0.0)])
+def test_sweep_size_1024_errors(storage, scale):
+    """Accuracy of the throughput sweep at N = 1024 (Taylor-Green, U0 = 0.01,
+    200 steps, the sweep's launch configuration: one node per thread at FP32,
+    four nodes per thread at 16 bit, FP16 scale 2^10): relative-L2 errors of u,
+    phi, S and omega against the FP64 oracle.  FP32: u and phi within 1e-5; S
+    and omega within 1e-5 or three times the error of the oracle's own
+    FP32-storage emulation (at this size storage rounding alone gives S 7.5e-6
+    and omega 1.8e-4: the velocity gradients are U0 k = 6e-5).  16 bit: every
+    field within three times the emulation of the same storage and scale; at
+    FP16 u and phi also within 2e-3.  Measured: FP32 u 8.1e-8, phi 2.8e-8,
+    S 1.17e-5, omega 3.2e-4; FP16 u 8.4e-4, phi 2.5e-4, S 6.2e-2, omega 1.45;
+    BF16 u 4.7e-3, phi 4.7e-4, S 0.49, omega 11 (each on its emulated floor)."""
+    n, steps = 1024, 200
+    s = spec(n, n, storage=storage, scale=scale)
+    F = as_f32(inputs.taylor_green(n, 0.01, phi_amp=0.1))
+    g = D.Lattice(gpu_config(s)).init(F.rho, F.ux, F.uy, F.phi, F.grads).step(steps)
+    fg = {k: np64(v) for k, v in g.fields().items()}
+    if "ref" not in SWEEP_REF:
+        SWEEP_REF["ref"] = O.OracleLattice(oracle_params(s)).init(
+            F.rho, F.ux, F.uy, F.phi, F.grads).step(steps).fields()
+    fo = SWEEP_REF["ref"]
+    fe = O.OracleLattice(oracle_params(s, storage)).init(
+        F.rho, F.ux, F.uy, F.phi, F.grads).step(steps).fields()
+    e, floor = sweep_errors(fg, fo), sweep_errors(fe, fo)
+    print(storage, "N 1024 errors", {k: f"{v:.2e}" for k, v in e.items()},
+          "emulation", {k: f"{v:.2e}" for k, v in floor.items()})
+    for k, v in e.items():
+        if storage == "fp32":
+            bound = max(1e-5, 3 * floor[k]) if k in ("omega", "S") else 1e-5
+        else:
+            bound = 3 * floor[k] + 1e-7
+        assert v <= bound, (k, v, floor[k])
+    if storage == "fp16":
+        assert e["u"] < 2e-3 and e["phi"] < 2e-3
+
+
 # --------------------------------------------------------------- edge cases
 def test_zero_steps_and_scalar_mask():
     """n = 0 is a no-op; phi = 0 everywhere makes omega NaN while S stays finite."""
