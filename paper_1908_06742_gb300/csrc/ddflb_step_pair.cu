@@ -1,17 +1,18 @@
-// Fused step for 16-bit population storage, two adjacent nodes per thread.
+// Fused step for 16-bit population storage with several adjacent nodes per
+// thread (this file: two, k_step_pair, and four, k_step_quad).
 //
 // With FP16/BF16 storage a one-node-per-thread pull moves 2 bytes per memory
-// instruction, so the step is bound by instruction issue rather than by HBM.
-// Here each thread owns the pair of nodes (x0, x0 + 1), x0 even: every plane
-// is read as aligned 4-byte pairs; a plane pulled from x - 1 or x + 1 also
-// reads the aligned pair to the left (x0 - 2) or right (x0 + 2), whose other
-// half the neighbouring thread reads as well (served from L1); stores are
-// 4-byte pairs.  The
-// per-node arithmetic is exactly that of k_step (same device functions), so
-// results are bit-identical to the one-node kernel.
+// access; 36 such streams per node reach only about 0.7 of the HBM copy
+// bandwidth even with no arithmetic (4-byte accesses about 0.83, aligned
+// 8-byte accesses about 0.93).  In k_step_pair each thread owns the pair of
+// nodes (x0, x0 + 1), x0 even: every plane is read as aligned 4-byte pairs; a
+// plane pulled from x - 1 or x + 1 also reads the aligned pair to the left
+// (x0 - 2) or right (x0 + 2), whose other half the neighbouring thread reads as
+// well (served from L1); stores are 4-byte pairs.  The per-node arithmetic is
+// exactly that of k_step (same device functions), so results are
+// bit-identical to the one-node kernel.
 //
-// Requirements: nx even, blockDim.x a multiple of 32 (a warp covers 64
-// consecutive nodes of one row).
+// Requirements: nx even (k_step_pair), nx a multiple of 4 (k_step_quad).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -335,8 +336,7 @@ cudaError_t launch_step_quad(const Launch& L, const void* fin, const void* gin, 
 }
 
 bool pair_step_eligible(const Launch& L) {
-  return !L.force && L.P.smodel < 2 && L.storage != 0 && L.P.nx % 2 == 0 &&
-         L.block.x % 32 == 0;
+  return !L.force && L.P.smodel < 2 && L.storage != 0 && L.P.nx % 2 == 0;
 }
 
 cudaError_t launch_step_pair(const Launch& L, const void* fin, const void* gin, void* fout,
