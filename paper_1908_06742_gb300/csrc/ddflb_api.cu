@@ -5,6 +5,7 @@
 // I/O, checkpoints and thread-local error messages.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -188,6 +189,10 @@ struct ddflb_ctx {
   float* stage_out;   // output staging area (host I/O)
   cudaStream_t io_up, io_down;  // streams of host uploads / downloads (null: the context stream)
   cudaEvent_t ev_in_free, ev_in_ready, ev_out_ready, ev_out_free;  // host-I/O ordering
+  // kGraphSteps steps captured as one CUDA graph, starting from pops[0] / pops[1]
+  // (null: not built yet); graph_failed: capture unavailable, launch step by step
+  cudaGraphExec_t step_graph[2];
+  bool graph_failed;
 };
 
 namespace {
@@ -224,6 +229,55 @@ cudaError_t run_step(const ddflb_ctx* c, const void* fin, const void* gin, void*
   if (pair && pair_step_eligible(c->L))
     return launch_step_pair(c->L, fin, gin, fout, gout, c->status);
   return launch_step(c->L, fin, gin, fout, gout, c->status);
+}
+
+// Small lattices are launch-bound: runs of kGraphSteps steps between checks
+// replay one captured graph (an even count, so the buffer parity returns).
+// Only without a time-modulated force (whose factor changes every step).
+constexpr int kGraphSteps = 64;
+
+void drop_graphs(ddflb_ctx* c) {
+  for (cudaGraphExec_t& g : c->step_graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+// The graph of kGraphSteps steps that starts from pops[c->cur], built on first
+// use (null if capture is unavailable: the caller then launches step by step).
+cudaGraphExec_t step_graph(ddflb_ctx* c) {
+  const int p = c->cur;
+  if (c->step_graph[p] || c->graph_failed) return c->step_graph[p];
+  cudaStream_t cs;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    c->graph_failed = true;
+    return nullptr;
+  }
+  const cudaStream_t saved = c->L.stream;
+  c->L.stream = cs;
+  cudaGraph_t g = nullptr;
+  bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  for (int i = 0, cur = p; ok && i < kGraphSteps; ++i, cur ^= 1) {
+    char* fo = (char*)c->pops[cur ^ 1];
+    const size_t gofs = 9 * c->lay.pitch * (size_t)c->p.ny * elem_size(c->p.storage);
+    ok = run_step(c, c->pops[cur], (const char*)c->pops[cur] + gofs, fo, fo + gofs) ==
+         cudaSuccess;
+  }
+  if (cudaStreamEndCapture(cs, &g) != cudaSuccess) ok = false;
+  c->L.stream = saved;
+  cudaGraphExec_t ex = nullptr;
+  if (ok && cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) ok = false;
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  cudaGetLastError();  // clear a capture error, if any
+  if (!ok) {
+    c->graph_failed = true;
+    return nullptr;
+  }
+  c->step_graph[p] = ex;
+  return ex;
 }
 }  // namespace
 
@@ -381,7 +435,27 @@ ddflb_status ddflb_init_host(ddflb_ctx* c, const float* rho, const float* ux, co
 ddflb_status ddflb_step(ddflb_ctx* c, int64_t n) {
   if (!c) return fail(DDFLB_EINVAL, "NULL handle");
   if (n < 0) return fail(DDFLB_EINVAL, "n < 0");
-  for (int64_t i = 0; i < n; ++i) {
+  const int K = c->p.check_every;
+  while (n > 0) {
+    if (c->p.force_omega == 0.0 && !c->graph_failed) {
+      // whole graphs up to the next check step (checks run after it, as below)
+      const int64_t until = K > 0 ? std::min<int64_t>(n, K - c->step % K) : n;
+      const int64_t reps = until / kGraphSteps;
+      at_time(c, c->step);  // (the factor is 1 at every step here)
+      cudaGraphExec_t ex = reps > 0 ? step_graph(c) : nullptr;
+      if (ex) {
+        for (int64_t r = 0; r < reps; ++r) {
+          cudaError_t e = cudaGraphLaunch(ex, c->L.stream);
+          if (e != cudaSuccess) return cuda_fail(e, "step graph");
+        }
+        c->step += reps * kGraphSteps;
+        n -= reps * kGraphSteps;
+        ddflb_status s = checks_at(c);
+        if (s != DDFLB_OK) return s;
+        continue;
+      }
+    }
+    --n;
     const int src = c->cur, dst = c->cur ^ 1;
     void* fo = c->pops[dst];
     void* go = (char*)fo + 9 * c->lay.pitch * (size_t)c->p.ny * elem_size(c->p.storage);
@@ -528,6 +602,7 @@ ddflb_status ddflb_set_state(ddflb_ctx* c, const void* src, size_t bytes, int64_
 }
 
 ddflb_status ddflb_destroy(ddflb_ctx* c) {
+  if (c) drop_graphs(c);
   if (c && c->ev_in_free) {
     cudaEvent_t evs[4] = {c->ev_in_free, c->ev_in_ready, c->ev_out_ready, c->ev_out_free};
     for (cudaEvent_t ev : evs)
@@ -593,6 +668,7 @@ ddflb_status ddflb_autotune(ddflb_ctx* c, int32_t trial_steps, int32_t* block_x,
   if (e != cudaSuccess) return cuda_fail(e, "autotune trial");
   c->L.block = bestb;
   c->path = bestp;
+  drop_graphs(c);
   if (path) *path = bestp;
   e = cudaMemsetAsync(c->pops[0], 0, 2 * c->lay.pops_bytes, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -611,6 +687,7 @@ ddflb_status ddflb_autotune(ddflb_ctx* c, int32_t trial_steps, int32_t* block_x,
 ddflb_status ddflb_set_path(ddflb_ctx* c, int32_t path) {
   if (!c || path < 0 || path > 3) return fail(DDFLB_EINVAL, "path must be 0, 1, 2 or 3");
   c->path = path;
+  drop_graphs(c);
   return DDFLB_OK;
 }
 
@@ -618,6 +695,7 @@ ddflb_status ddflb_set_force_field(ddflb_ctx* c, const float* dev_field) {
   if (!c) return fail(DDFLB_EINVAL, "NULL handle");
   c->L.P.ffield = dev_field;
   c->L.force = has_force(c->p, dev_field);
+  drop_graphs(c);
   return DDFLB_OK;
 }
 
@@ -628,6 +706,7 @@ ddflb_status ddflb_set_block(ddflb_ctx* c, int32_t block_x, int32_t block_y) {
     return fail(DDFLB_EINVAL, "block %d x %d: x a multiple of 32, 32..256 threads", block_x,
                 block_y);
   c->L.block = dim3(block_x, block_y, 1);
+  drop_graphs(c);
   return DDFLB_OK;
 }
 
