@@ -234,15 +234,22 @@ def step_kernel_name(args):
 
 
 def traffic_per_launch(args, n_cells):
-    """DRAM bytes per k_step launch from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
+    """DRAM bytes per step-kernel launch from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    return traffic_record(f"{step_kernel_name(args)}_{args.storage}" + (
+        "" if args.scalar_model == "mrt" else f"_{args.scalar_model}"), n_cells)
+
+
+def traffic_record(key, n_units):
+    """DRAM bytes per node (node-step for the batch) recorded by ncu in
+    profiles/traffic.json under `key`, times n_units; None if there is no record
+    or the kernel sources changed since it was taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
         import hashlib
-        e = d.get(f"{step_kernel_name(args)}_{args.storage}" + (
-            "" if args.scalar_model == "mrt" else f"_{args.scalar_model}"))
+        e = d.get(key)
         if not e:
             return None
         h = hashlib.sha256()
@@ -251,7 +258,7 @@ def traffic_per_launch(args, n_cells):
                 h.update(fh.read())
         if e.get("source_sha256") != h.hexdigest():
             return None
-        return e["dram_bytes_per_cell"] * n_cells
+        return e["dram_bytes_per_cell"] * n_units
     except Exception:
         return None
 
@@ -472,7 +479,11 @@ def run_batch(args, world, rank, local):
                    "cells": cells, "tiles": tune, "l2": f"{288 * cells / 1e9:.1f} GB of populations"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_kind": kind, "kernel": "k_batch",
-                     "traffic": None},
+                     # bytes per node-step from a 64-cavity capture, times this launch's
+                     # node-steps (traffic grows in proportion: every node-step moves the
+                     # same 18 planes)
+                     "algorithmic_bytes_per_launch": 144 * cells * lb,
+                     "traffic": traffic_record("k_batch_fp32", cells * lb)},
         "cpu_baseline": None, "e2e": e2e,
         "gpu_launches": args.steps,
         "clocks": clk,
