@@ -235,6 +235,18 @@ ddflb_status ddflb_populations(ddflb_ctx* c, float* f, float* g);
  * Returns EDIVERGED once a non-finite sum has been seen. */
 ddflb_status ddflb_stats(ddflb_ctx* c, double* mass, double* scalar, double* residual,
                          int64_t* step);
+/* Advance until steady state (Sec. 5.4 reports the cavity flows at steady
+ * state): steps up to each residual check (the context's check_every K must be
+ * > 0) and reads r = |u(t) - u(t-K)| / (K |u(t)|) from the check, as
+ * ddflb_stats reports it.  Returns OK as soon as r < tol; EDIVERGED once a
+ * non-finite sum is seen; ENOTCONVERGED after max_steps steps, or when
+ * stall_checks > 0 consecutive checks have not lowered r below its best value
+ * so far (the residual has reached its precision floor above tol).  Steps
+ * taken by this call go to *steps_taken (may be NULL).  Synchronises the
+ * context stream at every check.  Errors: EINVAL (check_every <= 0, tol <= 0,
+ * negative counts). */
+ddflb_status ddflb_run_to_tolerance(ddflb_ctx* c, double tol, int64_t max_steps,
+                                    int32_t stall_checks, int64_t* steps_taken);
 
 /* Checkpoint: size in bytes of the raw state, and copies of it to/from a
  * caller device buffer (device-to-device, asynchronous).  Resuming from a saved

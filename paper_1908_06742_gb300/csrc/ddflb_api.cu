@@ -4,6 +4,7 @@
 // all device memory), the step loop with its periodic reductions, host-staged
 // I/O, checkpoints and thread-local error messages.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -196,6 +197,14 @@ struct ddflb_ctx {
 };
 
 namespace {
+// NVTX range over one host call (visible in profilers; a no-op without one)
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
+
 // Body-force modulation cos(force_omega t) for the launches that act on the
 // state at time t (the collision of step t, and fields / sums of state t).
 void at_time(ddflb_ctx* c, int64_t t) {
@@ -373,6 +382,7 @@ ddflb_status ddflb_create(const ddflb_params* p, void* ws, size_t bytes, void* s
 ddflb_status ddflb_init(ddflb_ctx* c, const float* rho, const float* ux, const float* uy,
                         const float* phi, const float* grads) {
   if (!c || !rho || !ux || !uy || !phi) return fail(DDFLB_EINVAL, "NULL handle or field");
+  Range range("ddflb_init");
   if (grads) {
     const double* wf = c->p.omega_f;
     const float* wg = c->L.P.wg;
@@ -435,6 +445,7 @@ ddflb_status ddflb_init_host(ddflb_ctx* c, const float* rho, const float* ux, co
 ddflb_status ddflb_step(ddflb_ctx* c, int64_t n) {
   if (!c) return fail(DDFLB_EINVAL, "NULL handle");
   if (n < 0) return fail(DDFLB_EINVAL, "n < 0");
+  Range range("ddflb_step");
   const int K = c->p.check_every;
   while (n > 0) {
     if (c->p.force_omega == 0.0 && !c->graph_failed) {
@@ -444,6 +455,7 @@ ddflb_status ddflb_step(ddflb_ctx* c, int64_t n) {
       at_time(c, c->step);  // (the factor is 1 at every step here)
       cudaGraphExec_t ex = reps > 0 ? step_graph(c) : nullptr;
       if (ex) {
+        Range graphs("ddflb_step graph replay");
         for (int64_t r = 0; r < reps; ++r) {
           cudaError_t e = cudaGraphLaunch(ex, c->L.stream);
           if (e != cudaSuccess) return cuda_fail(e, "step graph");
@@ -473,6 +485,7 @@ ddflb_status ddflb_step(ddflb_ctx* c, int64_t n) {
 ddflb_status ddflb_fields(ddflb_ctx* c, float* rho, float* ux, float* uy, float* phi, float* sxx,
                           float* sxy, float* syy, float* omega) {
   if (!c) return fail(DDFLB_EINVAL, "NULL handle");
+  Range range("ddflb_fields");
   FieldPtrs fp{{rho, ux, uy, phi, sxx, sxy, syy, omega}};
   at_time(c, c->step);
   return check_launch(launch_fields(c->L, fptr(c, c->cur), gptr(c, c->cur), fp), "fields");
@@ -574,6 +587,49 @@ ddflb_status ddflb_stats(ddflb_ctx* c, double* mass, double* scalar, double* res
   if (h.diverged) return fail(DDFLB_EDIVERGED, "non-finite mass/scalar sum by step %lld",
                               (long long)c->step);
   return DDFLB_OK;
+}
+
+// Run to steady state (Sec. 5.4 reports the cavity flows at steady state):
+// steps in chunks up to each check and reads the residual the check left in
+// the status block.
+ddflb_status ddflb_run_to_tolerance(ddflb_ctx* c, double tol, int64_t max_steps,
+                                    int32_t stall_checks, int64_t* steps_taken) {
+  if (steps_taken) *steps_taken = 0;
+  if (!c) return fail(DDFLB_EINVAL, "NULL handle");
+  const int K = c->p.check_every;
+  if (K <= 0) return fail(DDFLB_EINVAL, "run_to_tolerance needs check_every > 0");
+  if (!(tol > 0.0) || max_steps < 0 || stall_checks < 0)
+    return fail(DDFLB_EINVAL, "tol must be > 0, max_steps and stall_checks >= 0");
+  Range range("ddflb_run_to_tolerance");
+  double best = INFINITY;
+  int since_best = 0;
+  int64_t done = 0;
+  while (done < max_steps) {
+    const int64_t n = std::min<int64_t>(max_steps - done, K - c->step % K);
+    ddflb_status s = ddflb_step(c, n);
+    if (s != DDFLB_OK) return s;
+    done += n;
+    if (steps_taken) *steps_taken = done;
+    if (c->step % K != 0) continue;  // the step limit ended the chunk before a check
+    DevStatus h{};
+    cudaError_t e = cudaMemcpyAsync(&h, c->status, sizeof h, cudaMemcpyDeviceToHost, c->L.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->L.stream);
+    if (e != cudaSuccess) return cuda_fail(e, "run_to_tolerance");
+    if (h.diverged)
+      return fail(DDFLB_EDIVERGED, "non-finite mass/scalar sum by step %lld", (long long)c->step);
+    if (!h.has_residual) continue;  // the first check only takes the snapshot
+    const double r = h.residual / K;
+    if (r < tol) return DDFLB_OK;
+    if (r < best) {
+      best = r;
+      since_best = 0;
+    } else if (stall_checks > 0 && ++since_best >= stall_checks) {
+      return fail(DDFLB_ENOTCONVERGED,
+                  "residual %.3g stalled: no check below its best %.3g for %d checks (step %lld)",
+                  r, best, stall_checks, (long long)c->step);
+    }
+  }
+  return fail(DDFLB_ENOTCONVERGED, "residual above %g after %lld steps", tol, (long long)done);
 }
 
 size_t ddflb_state_bytes(const ddflb_ctx* c) { return c ? c->lay.pops_bytes : 0; }

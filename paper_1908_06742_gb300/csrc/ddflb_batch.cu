@@ -17,6 +17,7 @@
 // The chunk launch reads the current step from device memory, so one captured
 // CUDA graph of the launch replays for every chunk.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -679,6 +680,11 @@ ddflb_status ddflb_batch_init(ddflb_batch* b, int32_t i, const float* rho, const
 ddflb_status ddflb_batch_step(ddflb_batch* b, int64_t n) {
   if (!b) return bfail(DDFLB_EINVAL, "NULL batch");
   if (n < 0) return bfail(DDFLB_EINVAL, "n < 0");
+  // one NVTX range over the call's chunk launches (graph replays)
+  nvtxRangePushA("ddflb_batch_step");
+  struct PopRange {
+    ~PopRange() { nvtxRangePop(); }
+  } pop_range;
   int64_t left = n;
   while (left > 0) {
     const int k = (int)std::min<int64_t>(left, b->chunk);

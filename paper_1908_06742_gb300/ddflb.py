@@ -70,6 +70,8 @@ SIGNATURES = {
     "ddflb_set_io_streams": (ctypes.c_int, [_VP, _VP, _VP]),
     "ddflb_io_wait": (ctypes.c_int, [_VP]),
     "ddflb_populations": (ctypes.c_int, [_VP, _FP, _FP]),
+    "ddflb_run_to_tolerance": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_int64, ctypes.c_int32,
+                                              ctypes.POINTER(ctypes.c_int64)]),
     "ddflb_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double),
@@ -336,6 +338,19 @@ class Lattice:
         f, g = self._empty(9), self._empty(9)
         _check(self.lib.ddflb_populations(self._h, f.data_ptr(), g.data_ptr()))
         return f, g
+
+    def run_to_tolerance(self, tol: float = 1e-8, max_steps: int = 10_000_000,
+                         stall_checks: int = 0) -> dict:
+        """Step until the residual (checked every check_every steps) is below
+        tol.  Returns {"status": "OK" | "ENOTCONVERGED" | "EDIVERGED", "steps": n,
+        "message": ...}; other errors raise."""
+        k = ctypes.c_int64()
+        st = self.lib.ddflb_run_to_tolerance(self._h, float(tol), int(max_steps),
+                                             int(stall_checks), ctypes.byref(k))
+        if st not in (OK, ENOTCONVERGED, EDIVERGED):
+            _check(st)
+        return {"status": STATUS_NAMES[st], "steps": k.value,
+                "message": "" if st == OK else self.lib.ddflb_last_error().decode()}
 
     def stats(self) -> dict:
         m, s, r = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()

@@ -86,6 +86,10 @@ def test_grid_size_limit(lib):
     assert n >= 2 * 18 * 65536 * 65535 * 2
 
 
+def test_run_to_tolerance_rejects_null_handle(lib):
+    assert lib.ddflb_run_to_tolerance(None, 1e-8, 10, 0, None) == D.EINVAL
+
+
 def test_conserved_rates_must_be_zero(lib):
     c = good(); c.omega_f = (0, 0.5, 0, 1.2, 1.5, 1.5, 1, 1, 1)
     p = c.to_c()

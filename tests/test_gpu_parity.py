@@ -267,6 +267,56 @@ def test_16bit_storage_taylor_green(storage, scale):
         assert e["u"] < 2e-3 and e["phi"] < 2e-3
 
 
+# --------------------------------------------------------------- run to steady state
+def cavity_cfg(n, re, check_every=100):
+    U = 0.1
+    w = 1.0 / (3.0 * U * n / re + 0.5)
+    return D.Config(nx=n, ny=n, bc="cavity", u_lid=U, phi_lid=1.0, phi_wall=0.0,
+                    omega_f=(0, 0, 0, 1.2, w, w, 1.2, 1.2, 1.2),
+                    omega_g=(0, w, w, 1.2, 1.2, 1.2, 1.2, 1.2, 1.2), check_every=check_every)
+
+
+def test_run_to_tolerance_matches_batch_freeze():
+    """A 64^2 cavity (Re 100) run to residual 1e-8 stops at the same check as
+    the batched step freezes the same cavity (bit-identical paths, same
+    residual definition); a step limit below that returns ENOTCONVERGED."""
+    cfg = cavity_cfg(64, 100.0)
+    F = inputs.rest(64, 64, phi=0.0)
+    lat = D.Lattice(cfg).init(F.rho, F.ux, F.uy, F.phi)
+    r = lat.run_to_tolerance(1e-8, 2_000_000)
+    assert r["status"] == "OK", r
+    assert r["steps"] % 100 == 0 and lat.stats()["residual"] < 1e-8
+    b = D.Batch([cfg]).set_run(tol=1e-8, steps_per_launch=1000)
+    b.init(0, F.rho, F.ux, F.uy, F.phi)
+    for _ in range(r["steps"] // 1000 + 2):
+        b.step(1000)
+    st = b.stats()
+    assert st["flags"][0] == D.INST_CONVERGED and st["steps_to_tol"][0] == r["steps"], (st, r)
+    lat2 = D.Lattice(cfg).init(F.rho, F.ux, F.uy, F.phi)
+    short = lat2.run_to_tolerance(1e-8, r["steps"] - 1000)
+    assert short["status"] == "ENOTCONVERGED" and short["steps"] == r["steps"] - 1000
+    assert "after" in short["message"]
+
+
+def test_run_to_tolerance_detects_a_stall():
+    """An unreachable tolerance: the residual of a 16^2 cavity (Re 10) falls to
+    its FP32 floor and stops improving; five checks without a new best end the
+    run with ENOTCONVERGED long before the step limit."""
+    cfg = cavity_cfg(16, 10.0)
+    F = inputs.rest(16, 16, phi=0.0)
+    lat = D.Lattice(cfg).init(F.rho, F.ux, F.uy, F.phi)
+    r = lat.run_to_tolerance(1e-30, 2_000_000, stall_checks=5)
+    print(r)
+    assert r["status"] == "ENOTCONVERGED" and "stalled" in r["message"]
+    assert r["steps"] < 2_000_000
+
+
+def test_run_to_tolerance_needs_checks():
+    lat = D.Lattice(cavity_cfg(16, 10.0, check_every=0))
+    with pytest.raises(D.DdflbError):
+        lat.run_to_tolerance(1e-8, 100)
+
+
 # --------------------------------------------------------------- throughput-sweep accuracy
 SWEEP_REF = {}
 
