@@ -179,6 +179,62 @@ def test_c4_batch_sampled_instances_vs_oracle():
         assert e_u < 1e-5 and e_phi < 1e-5 and e_s < 1e-5, (n, e_u, e_phi, e_s)
 
 
+def test_c4_long_run_small_instances_vs_oracle():
+    """The batched-cavity recipe (seed 0, first 64 draws: all sizes mixed in one
+    persistent launch) run for the full 20000 steps; the first 64^2, 96^2 and
+    128^2 instances against the FP64 oracle: u, phi and S within 1e-5 or three
+    times the error of the oracle's own FP32-storage emulation, omega likewise
+    where |phi| > 2e-3 (phi = 0 on three walls)."""
+    draws = inputs.cavity_batch(64, seed=0)
+    cfgs = []
+    for d in draws:
+        n, U = d["n"], 0.1
+        w, wg = rate(U * n / d["re"]), rate(U * n / d["pe"])
+        cfgs.append(D.Config(nx=n, ny=n, bc="cavity", u_lid=U, phi_lid=1.0, phi_wall=0.0,
+                             omega_f=(0, 0, 0, 1.2, w, w, 1.2, 1.2, 1.2),
+                             omega_g=(0, wg, wg, 1.2, 1.2, 1.2, 1.2, 1.2, 1.2), check_every=100))
+    b = D.Batch(cfgs).set_run(tol=0.0, steps_per_launch=1000)
+    for i, c in enumerate(cfgs):
+        F = inputs.rest(c.nx, c.ny, phi=0.0)
+        b.init(i, F.rho, F.ux, F.uy, F.phi)
+    steps = 20000
+    b.step(steps)
+    assert b.stats()["status"] == D.OK
+    picks = {}
+    for i, d in enumerate(draws):
+        if d["n"] in (64, 96, 128):
+            picks.setdefault(d["n"], i)
+    assert len(picks) == 3, sorted(picks)
+
+    def errs(got, ref, sel):
+        e = {"u": math.sqrt(np.sum((got["ux"] - ref["ux"]) ** 2 + (got["uy"] - ref["uy"]) ** 2) /
+                            np.sum(ref["ux"] ** 2 + ref["uy"] ** 2)),
+             "phi": math.sqrt(np.sum((got["phi"] - ref["phi"]) ** 2) / np.sum(ref["phi"] ** 2))}
+        srms = max(math.sqrt(np.mean(ref[k] ** 2)) for k in ("sxx", "sxy", "syy"))
+        e["S"] = max(math.sqrt(np.mean((got[k] - ref[k]) ** 2)) for k in ("sxx", "sxy", "syy")) / srms
+        e["omega"] = math.sqrt(np.sum((got["omega"][sel] - ref["omega"][sel]) ** 2) /
+                               np.sum(ref["omega"][sel] ** 2))
+        return e
+
+    for n, i in sorted(picks.items()):
+        c = cfgs[i]
+        wf, wg = c.rates()
+        F = inputs.rest(n, n, phi=0.0)
+        out = []
+        for storage in ("fp64", "fp32"):
+            p = O.OracleParams(nx=n, ny=n, bc="cavity", lam_override=wf, lam_phi_override=wg,
+                               u_lid=c.u_lid, phi_lid=1.0, phi_wall=0.0, storage=storage)
+            out.append(O.OracleLattice(p).init(F.rho, F.ux, F.uy, F.phi).step(steps).fields())
+        ref, emu = out
+        sel = np.abs(ref["phi"]) > 2e-3
+        got = {k: np64(v) for k, v in b.fields(i).items()}
+        e, floor = errs(got, ref, sel), errs(emu, ref, sel)
+        print(n, "errors", {k: f"{v:.2e}" for k, v in e.items()},
+              "floor", {k: f"{v:.2e}" for k, v in floor.items()})
+        for k, v in e.items():
+            assert v <= max(1e-5, 3 * floor[k]), (n, k, v, floor[k])
+
+
 def test_barrier_wait_runs_out_and_reports_timeout():
     """One CTA never arrives (a flag nothing sets): the others give up after the
     bounded wait, the launch ends, stats reports ETIMEOUT, and the context stays
