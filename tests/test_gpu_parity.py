@@ -298,6 +298,44 @@ def test_run_to_tolerance_matches_batch_freeze():
     assert "after" in short["message"]
 
 
+def test_cavity_256_steady_state_vs_oracle():
+    """The cavity workload's Re 100 case (256^2, lid 0.1, Pe = Re, phi = 1 on the
+    lid and 0 elsewhere): the GPU runs to residual 1e-8 (52000 steps), the FP64
+    oracle runs the same number of steps; u, phi, S and omega (where
+    |phi| > 2e-3) within 1e-5 or three times the error of the oracle's own
+    FP32-storage emulation.  About 100 s of oracle time."""
+    n, re = 256, 100.0
+    cfg = cavity_cfg(n, re, check_every=1000)
+    F = inputs.rest(n, n, phi=0.0)
+    lat = D.Lattice(cfg).init(F.rho, F.ux, F.uy, F.phi)
+    r = lat.run_to_tolerance(1e-8, 400_000)
+    assert r["status"] == "OK", r
+    steps = r["steps"]
+    wf, wg = cfg.rates()
+    out = []
+    for storage in ("fp64", "fp32"):
+        p = O.OracleParams(nx=n, ny=n, bc="cavity", lam_override=wf, lam_phi_override=wg,
+                           u_lid=cfg.u_lid, phi_lid=1.0, phi_wall=0.0, storage=storage)
+        out.append(O.OracleLattice(p).init(F.rho, F.ux, F.uy, F.phi).step(steps).fields())
+    ref, emu = out
+    sel = np.abs(ref["phi"]) > 2e-3
+    got = {k: np64(v) for k, v in lat.fields().items()}
+
+    def errs(a):
+        e = {"u": rel_l2(np.stack([a["ux"], a["uy"]]), np.stack([ref["ux"], ref["uy"]])),
+             "phi": rel_l2(a["phi"], ref["phi"]),
+             "omega": rel_l2(a["omega"][sel], ref["omega"][sel])}
+        srms = max(math.sqrt(np.mean(ref[k] ** 2)) for k in ("sxx", "sxy", "syy"))
+        e["S"] = max(math.sqrt(np.mean((a[k] - ref[k]) ** 2)) for k in ("sxx", "sxy", "syy")) / srms
+        return e
+
+    e, floor = errs(got), errs(emu)
+    print("cavity 256 Re 100 steady,", steps, "steps:", {k: f"{v:.2e}" for k, v in e.items()},
+          "floor", {k: f"{v:.2e}" for k, v in floor.items()})
+    for k, v in e.items():
+        assert v <= max(1e-5, 3 * floor[k]), (k, v, floor[k])
+
+
 def test_run_to_tolerance_detects_a_stall():
     """An unreachable tolerance: the residual of a 16^2 cavity (Re 10) falls to
     its FP32 floor and stops improving; five checks without a new best end the
