@@ -533,6 +533,7 @@ def run_cavity(args, world, rank, local):
         torch.cuda.synchronize(dev)
         steps, res_now = [0] * len(cfgs), [float("nan")] * len(cfgs)
         active = [True] * len(cfgs)
+        barrier(world)
         t0 = time.perf_counter()
         while any(active):
             for i, (lat, st) in enumerate(zip(lats, streams)):
@@ -551,9 +552,10 @@ def run_cavity(args, world, rank, local):
                     if res_now[i] < 1e-8 or steps[i] >= cap:
                         active[i] = False
         torch.cuda.synchronize(dev)
-        dt = time.perf_counter() - t0
+        barrier(world)
+        dt = max_over_ranks(world, time.perf_counter() - t0)
         if rep >= args.warmup:
-            runs.append((dt, sum(steps) * n * n, list(steps), list(res_now)))
+            runs.append((dt, world * sum(steps) * n * n, list(steps), list(res_now)))
     if rank != 0:
         return
     dt = sum(r[0] for r in runs)
