@@ -266,7 +266,7 @@ ddflb_status ddflb_set_state(ddflb_ctx* c, const void* dev_src, size_t bytes, in
  * held by every GPU that loads the library until the process exits).
  *   mode bit 1: also compute the residual |u - u_snap|_2 / |u|_2 against the
  *               snapshot stored by an earlier call (EINVAL if none of this
- *               grid size was stored on this device);
+ *               nx x ny grid was stored on this device);
  *   mode bit 2: store this state's velocity as the new snapshot.
  * dev_out: 4 device doubles (mass, scalar, sum |u|^2, residual or NaN).
  * Asynchronous on cuda_stream.  The first call on a device, with that device

@@ -790,8 +790,16 @@ __device__ __align__(256) NoallocScratch g_noalloc_scratch;
 
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mutex;
-NoallocScratch* g_noalloc_addr[kMaxDevices];     // device address, per device ordinal
-int64_t g_noalloc_snapshot_nodes[kMaxDevices];    // node count of the stored snapshot (0: none)
+NoallocScratch* g_noalloc_addr[kMaxDevices];  // device address, per device ordinal
+// grid of the stored velocity snapshot, per device ordinal ({0, 0}: none); the
+// snapshot is indexed by node, so a residual needs the same nx and ny
+int32_t g_noalloc_snapshot_grid[kMaxDevices][2];
+
+// Forget the snapshot of device `dev` (caller holds g_noalloc_mutex).
+void snap_clear(int dev) {
+  g_noalloc_snapshot_grid[dev][0] = 0;
+  g_noalloc_snapshot_grid[dev][1] = 0;
+}
 
 // Turns the status block into (mass, scalar, sum |u|^2, residual).
 __global__ void k_noalloc_out(const DevStatus* st, double cells, double rho0, double phi0,
@@ -839,10 +847,12 @@ extern "C" ddflb_status ddflb_reduce_noalloc(const ddflb_params* p, const void* 
       g_noalloc_addr[dev] = (NoallocScratch*)ptr;
     }
     scratch = g_noalloc_addr[dev];
-    if ((mode & 1) && g_noalloc_snapshot_nodes[dev] != nodes)
-      return fail(DDFLB_EINVAL, "no velocity snapshot of a %lld-node grid stored on device %d",
-                  (long long)nodes, dev);
-    if (mode & 2) g_noalloc_snapshot_nodes[dev] = nodes;
+    const int32_t* snap = g_noalloc_snapshot_grid[dev];
+    if ((mode & 1) && (snap[0] != p->nx || snap[1] != p->ny))
+      return fail(DDFLB_EINVAL, "no velocity snapshot of a %d x %d grid stored on device %d",
+                  p->nx, p->ny, dev);
+    // a snapshot about to be overwritten is no longer valid, whatever happens below
+    if (mode & 2) snap_clear(dev);
   }
   cudaStream_t st = (cudaStream_t)cuda_stream;
   Launch L;
@@ -859,6 +869,12 @@ extern "C" ddflb_status ddflb_reduce_noalloc(const ddflb_params* p, const void* 
   const char* g = f + 9 * (size_t)lay.pitch * p->ny * elem_size(p->storage);
   e = launch_reduce(L, f, g, scratch->uprev, mode, scratch->partials, &scratch->status);
   if (e != cudaSuccess) return cuda_fail(e, "no-allocation reduce");
+  if (mode & 2) {
+    // the snapshot counts as stored only once its writer was launched
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    g_noalloc_snapshot_grid[dev][0] = p->nx;
+    g_noalloc_snapshot_grid[dev][1] = p->ny;
+  }
   k_noalloc_out<<<1, 32, 0, st>>>(&scratch->status, (double)nodes, p->rho0, p->phi0, mode,
                                   dev_out);
   e = cudaGetLastError();

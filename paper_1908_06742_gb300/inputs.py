@@ -117,3 +117,22 @@ def cavity_batch(n_inst: int = 512, seed: int = 0, re_lo: float = 100.0, re_hi: 
     n = r.choice(np.asarray(sizes), size=n_inst)
     re = np.exp(r.uniform(math.log(re_lo), math.log(re_hi), size=n_inst))
     return [dict(n=int(n[i]), re=float(re[i]), pe=float(re[i])) for i in range(n_inst)]
+
+
+def sine_waves(n: int, a: float = 0.01, b: float = 0.008, c: float = 0.004, d: float = -0.003,
+               phi_amp: float = 0.0) -> Fields:
+    """Smooth periodic velocity with every gradient component nonzero:
+    u_x = a sin(ky) + c sin(kx), u_y = b sin(kx) + d sin(ky), k = 2 pi / n
+    (shear from a, b; divergence from c, d), rho = 1,
+    phi = 1 + phi_amp sin(kx) sin(ky), with the exact gradients."""
+    k = 2.0 * math.pi / n
+    x = np.arange(n, dtype=np.float64)[None, :]
+    y = np.arange(n, dtype=np.float64)[:, None]
+    sx, cx, sy, cy = np.sin(k * x), np.cos(k * x), np.sin(k * y), np.cos(k * y)
+    b2 = lambda v: np.ascontiguousarray(np.broadcast_to(v, (n, n)), np.float64)
+    ux = b2(a * sy + c * sx)
+    uy = b2(b * sx + d * sy)
+    phi = b2(1.0 + phi_amp * sx * sy)
+    grads = np.stack([b2(c * k * cx), b2(a * k * cy), b2(b * k * cx), b2(d * k * cy),
+                      b2(phi_amp * k * cx * sy), b2(phi_amp * k * sx * cy)])
+    return Fields(np.ones((n, n)), ux, uy, phi, grads)
