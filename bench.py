@@ -47,10 +47,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="tg",
-                    choices=["tg", "sweep", "batch", "cavity", "surrogate", "gemm"],
+                    choices=["tg", "sweep", "batch", "cavity", "surrogate", "gemm", "slabs"],
                     help="tg: Taylor-Green throughput point; sweep: Taylor-Green at N = 1024, "
                          "4096, 8192, 16384 for each storage; batch: 512 uneven cavities; "
-                         "cavity: 256^2 cavities run to steady state")
+                         "cavity: 256^2 cavities run to steady state; slabs: one lattice "
+                         "divided into y-slabs, one per rank, halos exchanged every step")
     ap.add_argument("--instances", type=int, default=512)
     ap.add_argument("--gemm-shape", default=None,
                     help="gemm workload: one M,N,K,splits shape instead of the U-Net set")
@@ -410,19 +411,18 @@ def run_ours(args, world, rank, local):
     print(json.dumps(line))
 
 
-def shard_indices(n_items: int, rank: int, world: int):
-    """The items rank `rank` of `world` owns: i = rank, rank + world, ...
-    Every item belongs to exactly one rank."""
-    return list(range(rank, n_items, world))
-
-
-def batch_configs(args, rank):
-    """512 lid-driven cavities: size uniform over {64..512}, Re log-uniform in
-    [100, 3200], Pe = Re, lid 0.1, FP32 (rank r draws with seed r: weak scaling)."""
+def batch_configs(args, rank, world):
+    """512 lid-driven cavities (seed 0): size uniform over {64..512}, Re
+    log-uniform in [100, 3200], Pe = Re, lid 0.1, FP32.  The instances are
+    partitioned over ranks (rank r advances r, r + N, ...): strong scaling.
+    Returns (global indices, configs) of this rank's instances."""
     from paper_1908_06742_gb300 import ddflb as D
     from paper_1908_06742_gb300 import inputs
+    from paper_1908_06742_gb300.distributed import shard_indices
+    draws = inputs.cavity_batch(args.instances, seed=0)
+    mine = shard_indices(len(draws), rank, world)
     cfgs = []
-    for d in inputs.cavity_batch(args.instances, seed=rank):
+    for d in (draws[i] for i in mine):
         n, U = d["n"], 0.1
         w = 1.0 / (3.0 * U * n / d["re"] + 0.5)          # nu = U L / Re, L = n
         wg = 1.0 / (3.0 * U * n / d["pe"] + 0.5)
@@ -430,7 +430,7 @@ def batch_configs(args, rank):
                              omega_f=(0, 0, 0, 1.2, w, w, 1.2, 1.2, 1.2),
                              omega_g=(0, wg, wg, 1.2, 1.2, 1.2, 1.2, 1.2, 1.2),
                              check_every=100))
-    return cfgs
+    return mine, cfgs
 
 
 def run_batch(args, world, rank, local):
@@ -443,8 +443,9 @@ def run_batch(args, world, rank, local):
     B.build()
     D.load()
     dev = torch.device("cuda", local)
+    from paper_1908_06742_gb300.distributed import gather_indexed
     lb = args.lb_steps if args.lb_steps != 200 else 1000
-    cfgs = batch_configs(args, rank)
+    mine, cfgs = batch_configs(args, rank, world)
     cells = sum(c.nx * c.ny for c in cfgs)
     stream = torch.cuda.Stream(dev)
     with torch.cuda.stream(stream):
@@ -470,11 +471,16 @@ def run_batch(args, world, rank, local):
         torch.cuda.synchronize(dev)
         barrier(world)
         clk = clocks.stop()
-        total_ms = max_over_ranks(world, sum(a.elapsed_time(c) for a, c in ev))
+        local_ms = sum(a.elapsed_time(c) for a, c in ev)
+        total_ms = max_over_ranks(world, local_ms)
         st = b.stats()
-        value = world * cells * lb * args.steps / (total_ms / 1e3) / 1e6
+        job_cells = sum_over_ranks(world, float(cells))      # all 512 instances
+        value = job_cells * lb * args.steps / (total_ms / 1e3) / 1e6
         peak, kind = peaks()
-        achieved = 144 * cells * lb * args.steps / (total_ms / 1e3) / 1e9
+        # this rank's kernel against this GPU's copy peak
+        achieved = 144 * cells * lb * args.steps / (local_ms / 1e3) / 1e9
+        # per-instance flags of the whole job, in global order, on rank 0
+        flags = gather_indexed({i: int(f) for i, f in zip(mine, st["flags"])}, world)
         e2e = None
         if not args.no_e2e:
             h_in = [{k: torch.from_numpy(np.ascontiguousarray(getattr(F, k), np.float32)).pin_memory()
@@ -490,7 +496,7 @@ def run_batch(args, world, rank, local):
                 h_out[i].copy_(b.fields(i, names=("omega",))["omega"], non_blocking=True)
             torch.cuda.synchronize(dev)
             dt = max_over_ranks(world, time.perf_counter() - t0)
-            e2e = {"value": round(world * cells * lb / dt / 1e6, 1), "unit": "MLUPS",
+            e2e = {"value": round(job_cells * lb / dt / 1e6, 1), "unit": "MLUPS",
                    "h2d_bytes_per_step": int(16 * cells), "d2h_bytes_per_step": int(4 * cells),
                    "steps": 1}
     if rank != 0:
@@ -499,11 +505,14 @@ def run_batch(args, world, rank, local):
         "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{len(cfgs)} lid-driven cavities, sizes 64..512, Re log-uniform "
-                               f"[100, 3200], Pe = Re, fp32, {lb} steps per benchmark step, "
-                               f"residual check every 100 steps",
-                   "cells": cells, "tiles": tune, "l2": f"{288 * cells / 1e9:.1f} GB of populations"},
+        "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{args.instances} lid-driven cavities, sizes 64..512, Re "
+                               f"log-uniform [100, 3200], Pe = Re, fp32, {lb} steps per "
+                               f"benchmark step, residual check every 100 steps",
+                   "parallelism": (f"instances partitioned over {world} ranks" if world > 1
+                                   else "single"),
+                   "cells": int(job_cells), "cells_rank0": cells, "tiles": tune,
+                   "l2": f"{288 * cells / 1e9:.1f} GB of populations on rank 0"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_kind": kind, "kernel": "k_batch",
                      # bytes per node-step from a 64-cavity capture, times this launch's
@@ -514,7 +523,8 @@ def run_batch(args, world, rank, local):
         "cpu_baseline": None, "e2e": e2e,
         "gpu_launches": args.steps,
         "clocks": clk,
-        "checks": {"flags_nonzero": int((st["flags"] != 0).sum()), "status": int(st["status"])},
+        "checks": {"flags_nonzero": int(sum(f != 0 for f in flags)), "instances": len(flags),
+                   "status": int(st["status"])},
     }
     print(json.dumps(line))
 
@@ -621,6 +631,85 @@ def run_cavity(args, world, rank, local):
         "converged": [bool(x < 1e-8) for x in res_now],
     }
     print(json.dumps(line))
+
+
+def run_slabs(args, world, rank, local):
+    """One periodic Taylor-Green lattice of n x (n N) nodes divided into N
+    y-slabs of n x n, one per rank (weak scaling).  Every time step each rank
+    advances its slab, packs the 3 populations x 2 lattices x n values that
+    cross each face, swaps them with its two neighbours (NCCL send/receive)
+    and unpacks them into its ghost rows.  With N = 1 the slab is the whole
+    lattice and nothing is exchanged."""
+    import torch
+    from paper_1908_06742_gb300 import build as B
+    from paper_1908_06742_gb300 import ddflb as D
+    from paper_1908_06742_gb300 import inputs
+    from paper_1908_06742_gb300.distributed import allreduce_sums, halo_exchange
+
+    B.build()
+    D.load()
+    dev = torch.device("cuda", local)
+    n, lb = args.n, args.lb_steps
+    ny = n * world
+    wf, wg = rates(0.01)
+    cfg = D.Config(nx=n, ny=ny, storage=args.storage, omega_f=wf, omega_g=wg,
+                   scale_f=2.0 ** 10 if args.storage == "fp16" else 0.0,
+                   scale_g=2.0 ** 10 if args.storage == "fp16" else 0.0)
+    y0 = rank * n
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        lat = D.Lattice(cfg, device=dev, stream=stream, rows=(y0, n))
+        T = inputs.taylor_green(n, 0.01, phi_amp=0.1, ny=ny, window=(0, y0, n, n), xp=torch,
+                                device=dev)
+        lat.init(*[a.float() for a in (T.rho, T.ux, T.uy, T.phi, T.grads)])
+        del T
+        elem = torch.int32 if args.storage == "fp32" else torch.int16
+        m = lat.halo_elems()
+        down = torch.empty(m, dtype=elem, device=dev)
+        up = torch.empty(m, dtype=elem, device=dev)
+
+        def one_step():
+            lat.step(1)
+            if world > 1:
+                lat.halo_pack(down, up)
+                # NCCL's stream waits for the current stream (the pack) and the
+                # current stream waits for the exchange (req.wait), no host sync
+                fb, fa = halo_exchange(down, up, world, rank, periodic=True)
+                lat.halo_unpack(fb, fa)
+
+        for _ in range(args.warmup * lb):
+            one_step()
+        torch.cuda.synchronize(dev)
+        clocks = ClockSampler(local)
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        clocks.start()
+        t0 = time.perf_counter()
+        for _ in range(args.steps * lb):
+            one_step()
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        barrier(world)
+        clk = clocks.stop()
+        dt = max_over_ranks(world, dt)
+        s = lat.sums()
+        mass_dev, _, _ = allreduce_sums([s["mass_dev"], s["scalar_dev"], s["u2"]], world,
+                                        device=dev)
+    if rank != 0:
+        return
+    value = n * ny * lb * args.steps / dt / 1e6
+    print(json.dumps({
+        "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"taylor-green {n}x{ny} divided into {world} y-slabs of {n}x{n}, "
+                               f"{args.storage} storage, {lb} fused steps per benchmark step, "
+                               f"halo exchange every step",
+                   "parallelism": f"y-slabs over {world} ranks" if world > 1 else "single",
+                   "timing": "host clock around the steps and exchanges"},
+        "clocks": clk, "gpu_launches": args.steps * lb * (3 if world > 1 else 1),
+        "checks": {"mass_dev": mass_dev}}))
 
 
 def run_surrogate(args, world, rank, local):
@@ -810,6 +899,8 @@ def main():
         run_gemm(args, world, rank, local)
     elif args.workload == "sweep":
         run_sweep(args, world, rank, local)
+    elif args.workload == "slabs":
+        run_slabs(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

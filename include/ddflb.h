@@ -316,6 +316,65 @@ ddflb_status ddflb_set_force_field(ddflb_ctx* c, const float* dev_field);
 ddflb_status ddflb_destroy(ddflb_ctx* c);
 
 /* ---------------------------------------------------------------------------
+ * One lattice divided into y-slabs.  The collide-and-stream update of Secs. 2
+ * and 3 is local: a node pulls the post-collision populations of its eight
+ * neighbours only, so a slab of rows can advance on its own if, before each
+ * step, the populations that cross its faces are copied in from the slabs
+ * beside it.  Per face and step that is 3 populations (those with e_y = +1
+ * going up, e_y = -1 going down) x 2 lattices x nx values.  Divided runs are
+ * bit-identical to the undivided lattice.
+ *
+ * A slab context is a ddflb_ctx for rows [y0, y0 + rows) of the lattice *p
+ * (p->ny is the whole lattice's height).  Its population buffers carry one
+ * ghost row on each face shared with another slab: both faces of a slab of a
+ * periodic lattice (unless rows = p->ny), the inner faces of a cavity or
+ * channel, whose walls stay with the bottom and top slabs.  Every ddflb_*
+ * call on a whole lattice applies to it, for its own rows: ddflb_init and
+ * ddflb_fields take and give [rows][nx] arrays, ddflb_set_force_field a
+ * [2][rows][nx] array, ddflb_stats and ddflb_sums sum its own nodes.  While
+ * it has a ghost row: check_every must be 0 (combine ddflb_sums over slabs
+ * instead), force_omega must be 0, and ddflb_step takes n <= 1.  The protocol
+ * is init, then per step: ddflb_step(slab, 1) on every slab, then refresh the
+ * ghost rows (ddflb_halo_exchange_local for slabs on one device, or
+ * ddflb_halo_pack -> send/receive -> ddflb_halo_unpack between processes).
+ * The init writes the first step's ghost values itself: no exchange before
+ * the first step.  Fields, populations and sums read the ghost rows, so they
+ * too follow an exchange.  16-bit storage steps node by node in a slab (bit-
+ * identical to the grouped kernels of a whole lattice).  Errors: EINVAL (rows
+ * outside the lattice, check_every != 0 or force_omega != 0 with a ghost
+ * row), ENOMEM, as ddflb_create. */
+size_t ddflb_slab_workspace_bytes(const ddflb_params* p, int32_t y0, int32_t rows);
+ddflb_status ddflb_slab_create(const ddflb_params* p, int32_t y0, int32_t rows, void* dev_workspace,
+                               size_t bytes, void* cuda_stream, ddflb_ctx** out);
+/* Elements of the storage type (4 bytes at FP32, 2 at 16 bit) in one face
+ * message: [6][nx] = flow then scalar, 3 populations each. */
+size_t ddflb_halo_elems(const ddflb_ctx* c);
+/* Copy the outgoing populations of the current state into device buffers of
+ * ddflb_halo_elems elements: dev_down gets directions 4, 7, 8 of the bottom
+ * row (for the slab below), dev_up directions 2, 5, 6 of the top row (for the
+ * slab above).  Either may be NULL; EINVAL for a face without a neighbour. */
+ddflb_status ddflb_halo_pack(ddflb_ctx* c, void* dev_down, void* dev_up);
+/* Write what the slab below sent up (dev_from_below) and what the slab above
+ * sent down (dev_from_above) into the ghost rows.  Either may be NULL. */
+ddflb_status ddflb_halo_unpack(ddflb_ctx* c, const void* dev_from_below,
+                               const void* dev_from_above);
+/* Every face of `parts` slabs of one lattice held on one device, given bottom
+ * to top (covering all rows, same stream, same step): one kernel copies each
+ * slab's outgoing rows straight into its neighbours' ghost rows (wrapping for
+ * a periodic lattice).  At most 64 slabs.  parts = 1 with a whole-lattice
+ * context is a no-op. */
+ddflb_status ddflb_halo_exchange_local(ddflb_ctx* const* slabs, int32_t parts);
+/* Reduce the current state now (FP64 sums over the context's own nodes) and
+ * synchronise: out[0] = sum (rho - rho0), out[1] = sum (phi - phi0),
+ * out[2] = sum |u|^2, out[3] = sum |u - u_snap|^2 (mode bit 1; NaN without).
+ * mode bit 2 stores this state's velocity as the new snapshot.  Summed over
+ * the slabs of a lattice these give its mass, scalar and the residual
+ * sqrt(sum out[3] / sum out[2]) / K for snapshots K steps apart (the same r as
+ * ddflb_step's checks).  Errors: EINVAL (mode bit 1 without a snapshot),
+ * EDIVERGED. */
+ddflb_status ddflb_sums(ddflb_ctx* c, int32_t mode, double* out);
+
+/* ---------------------------------------------------------------------------
  * Batched lattices: n independent lattice pairs (each its own ddflb_params:
  * size, boundary kind, rates, lid) advanced together.  Each chunk of steps is
  * one persistent cooperative launch that walks a flattened tile list of all
@@ -453,6 +512,24 @@ ddflb_status ddflb_nn_adam(float* w, const float* g, float* m, float* v, void* w
 /* y (BF16, stride csy) = x (FP32, stride csx), rows x C. */
 ddflb_status ddflb_nn_cast_bf16(const float* x, int64_t rows, int32_t C, int32_t csx, void* y,
                                 int32_t csy, void* stream);
+
+/* Initial fields for a learned warm start, computed on the device from the
+ * network's prediction pred ([ny][nx][cs] FP32, channels: 0 u_x / U, 1 u_y / U,
+ * 2 phi, 3 omega n / (U omega_scale) with n = nx, 4 (rho - 1) / U^2; cs >= 5):
+ * rho, ux, uy, phi ([ny][nx] each) and grads ([6][ny][nx]: d_x u_x, d_y u_x,
+ * d_x u_y, d_y u_y, d_x phi, d_y phi), ready for ddflb_init / ddflb_batch_init,
+ * which add the Chapman-Enskog non-equilibrium part of Secs. 2 and 3.  phi is
+ * clamped to [phi_lo, phi_hi]; the derivatives are central differences of the
+ * predicted u and phi (one-sided on the outer rows and columns), except that
+ * the antisymmetric part of the velocity gradient is the predicted vorticity:
+ * d_x u_y = S_xy + omega / 2, d_y u_x = S_xy - omega / 2 with S_xy from the
+ * differences.  Each operation is rounded once in a fixed order.  The paper
+ * has no network; this serves the warm start only.  Asynchronous on stream.
+ * Errors: EINVAL (NULL pointers, sizes, u_lid <= 0, phi_lo > phi_hi), ECUDA. */
+ddflb_status ddflb_warm_fields(const float* pred, int32_t nx, int32_t ny, int32_t cs,
+                               double u_lid, double omega_scale, double phi_lo, double phi_hi,
+                               float* rho, float* ux, float* uy, float* phi, float* grads,
+                               void* stream);
 
 /* Message of the last error on the calling thread ("" if none). */
 const char* ddflb_last_error(void);

@@ -45,17 +45,25 @@ size_t elem_size(int storage) { return storage == DDFLB_FP32 ? 4 : 2; }
 
 struct Layout {
   int pitch;
+  int ghost_lo, ghost_hi;  // 1 where a y-slab shares its bottom / top face with another slab
+  int buf_ny;              // rows of the population buffers: own rows + ghost rows
+  size_t gofs;             // bytes from a buffer's flow planes to its scalar planes
   size_t pops_bytes;  // one buffer: 2 lattices x 9 planes
   size_t off_a, off_b, off_uprev, off_part, off_status, off_stage, off_stage_out, total;
 };
 
 // Row pitch: a multiple of 64 elements keeps every row start 128-byte aligned
-// for 16-bit storage and 256-byte aligned for FP32.
-Layout layout(const ddflb_params* p) {
+// for 16-bit storage and 256-byte aligned for FP32.  p->ny is the number of
+// rows the context owns (the whole lattice, or one y-slab).
+Layout layout(const ddflb_params* p, int ghost_lo = 0, int ghost_hi = 0) {
   Layout L{};
   L.pitch = (int)align_up((size_t)p->nx, 64);
-  const size_t plane = (size_t)L.pitch * p->ny;
+  L.ghost_lo = ghost_lo;
+  L.ghost_hi = ghost_hi;
+  L.buf_ny = p->ny + ghost_lo + ghost_hi;
+  const size_t plane = (size_t)L.pitch * L.buf_ny;
   const size_t cells = (size_t)p->nx * p->ny;
+  L.gofs = 9 * plane * elem_size(p->storage);
   L.pops_bytes = align_up(2 * 9 * plane * elem_size(p->storage), kAlign);
   size_t o = 0;
   L.off_a = o; o += L.pops_bytes;
@@ -113,12 +121,14 @@ ddflb_status validate(const ddflb_params* p) {
   return DDFLB_OK;
 }
 
-LbParams make_lb(const ddflb_params* p, int pitch) {
+LbParams make_lb(const ddflb_params* p, int pitch, int ghost_lo = 0, int ghost_hi = 0) {
   LbParams P{};
   P.nx = p->nx;
-  P.ny = p->ny;
+  P.ny = p->ny + ghost_lo + ghost_hi;
+  P.y0 = ghost_lo;
+  P.y1 = ghost_lo + p->ny;
   P.pitch = pitch;
-  P.plane = (int64_t)pitch * p->ny;
+  P.plane = (int64_t)pitch * P.ny;
   for (int k = 0; k < 9; ++k) {
     P.wf[k] = (float)p->omega_f[k];
     // SRT (App. B): one rate for every non-conserved scalar moment
@@ -194,6 +204,8 @@ struct ddflb_ctx {
   // (null: not built yet); graph_failed: capture unavailable, launch step by step
   cudaGraphExec_t step_graph[2];
   bool graph_failed;
+  int32_t slab_y0;    // first global row of a y-slab context (0 for a whole lattice)
+  int32_t global_ny;  // rows of the whole lattice
 };
 
 namespace {
@@ -270,7 +282,7 @@ cudaGraphExec_t step_graph(ddflb_ctx* c) {
   bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
   for (int i = 0, cur = p; ok && i < kGraphSteps; ++i, cur ^= 1) {
     char* fo = (char*)c->pops[cur ^ 1];
-    const size_t gofs = 9 * c->lay.pitch * (size_t)c->p.ny * elem_size(c->p.storage);
+    const size_t gofs = c->lay.gofs;
     ok = run_step(c, c->pops[cur], (const char*)c->pops[cur] + gofs, fo, fo + gofs) ==
          cudaSuccess;
   }
@@ -300,9 +312,7 @@ ddflb_status reset_status(ddflb_ctx* c) {
   return e == cudaSuccess ? DDFLB_OK : cuda_fail(e, "status reset");
 }
 
-const void* gptr(const ddflb_ctx* c, int buf) {
-  return (const char*)c->pops[buf] + 9 * c->lay.pitch * (size_t)c->p.ny * elem_size(c->p.storage);
-}
+const void* gptr(const ddflb_ctx* c, int buf) { return (const char*)c->pops[buf] + c->lay.gofs; }
 
 ddflb_status check_launch(cudaError_t e, const char* where) {
   return e == cudaSuccess ? DDFLB_OK : cuda_fail(e, where);
@@ -338,21 +348,50 @@ size_t ddflb_workspace_bytes(const ddflb_params* p) {
   return layout(p).total;
 }
 
-ddflb_status ddflb_create(const ddflb_params* p, void* ws, size_t bytes, void* stream,
-                          ddflb_ctx** out) {
-  if (!out) return fail(DDFLB_EINVAL, "out is NULL");
-  *out = nullptr;
+}  // extern "C"
+
+namespace {
+// Geometry of a y-slab [y0, y0 + rows) of the lattice *p: the slab's own
+// parameters (ny = rows) and its ghost rows (one on each face shared with
+// another slab: both faces of a periodic lattice's slab, the inner faces of a
+// walled one).
+ddflb_status slab_geometry(const ddflb_params* p, int32_t y0, int32_t rows, ddflb_params* own,
+                           int* glo, int* ghi) {
   ddflb_status s = validate(p);
   if (s != DDFLB_OK) return s;
+  if (y0 < 0 || rows < 1 || (int64_t)y0 + rows > p->ny)
+    return fail(DDFLB_EINVAL, "slab rows [%d, %lld) outside 0..%d", y0, (long long)y0 + rows, p->ny);
+  *own = *p;
+  own->ny = rows;
+  const bool whole = rows == p->ny;
+  if (p->bc == DDFLB_BC_PERIODIC) {
+    *glo = *ghi = whole ? 0 : 1;
+  } else {
+    *glo = y0 > 0 ? 1 : 0;
+    *ghi = y0 + rows < p->ny ? 1 : 0;
+  }
+  if ((*glo || *ghi) && p->check_every != 0)
+    return fail(DDFLB_EINVAL, "a y-slab context reduces through ddflb_sums: check_every must be 0");
+  if ((*glo || *ghi) && p->force_omega != 0.0)
+    return fail(DDFLB_EINVAL, "y-slab contexts take steady forces only");
+  if (((int64_t)p->nx + 63) / 64 * 64 * ((int64_t)rows + *glo + *ghi) >= (int64_t)1 << 32)
+    return fail(DDFLB_EINVAL, "slab of %d x %d: a padded plane reaches 2^32 nodes", p->nx, rows);
+  return DDFLB_OK;
+}
+
+ddflb_status create_ctx(const ddflb_params* p, int glo, int ghi, int32_t y0, int32_t global_ny,
+                        void* ws, size_t bytes, void* stream, ddflb_ctx** out) {
   if (!ws) return fail(DDFLB_EINVAL, "workspace is NULL");
   if ((uintptr_t)ws % kAlign) return fail(DDFLB_EINVAL, "workspace not %zu-byte aligned", kAlign);
-  const Layout lay = layout(p);
+  const Layout lay = layout(p, glo, ghi);
   if (bytes < lay.total)
     return fail(DDFLB_ENOMEM, "workspace %zu bytes < %zu required", bytes, lay.total);
   ddflb_ctx* c = new (std::nothrow) ddflb_ctx();
   if (!c) return fail(DDFLB_ENOMEM, "host allocation of the handle failed");
   c->p = *p;
   c->lay = lay;
+  c->slab_y0 = y0;
+  c->global_ny = global_ny;
   c->ws = (char*)ws;
   c->pops[0] = c->ws + lay.off_a;
   c->pops[1] = c->ws + lay.off_b;
@@ -362,7 +401,7 @@ ddflb_status ddflb_create(const ddflb_params* p, void* ws, size_t bytes, void* s
   c->status = (DevStatus*)(c->ws + lay.off_status);
   c->stage = (p->flags & DDFLB_FLAG_HOST_IO) ? (float*)(c->ws + lay.off_stage) : nullptr;
   c->stage_out = (p->flags & DDFLB_FLAG_HOST_IO) ? (float*)(c->ws + lay.off_stage_out) : nullptr;
-  c->L.P = make_lb(p, lay.pitch);
+  c->L.P = make_lb(p, lay.pitch, glo, ghi);
   c->L.P_bc = p->bc;
   c->L.storage = p->storage;
   c->L.force = has_force(*p, nullptr);
@@ -377,6 +416,36 @@ ddflb_status ddflb_create(const ddflb_params* p, void* ws, size_t bytes, void* s
   }
   *out = c;
   return DDFLB_OK;
+}
+}  // namespace
+
+extern "C" {
+
+ddflb_status ddflb_create(const ddflb_params* p, void* ws, size_t bytes, void* stream,
+                          ddflb_ctx** out) {
+  if (!out) return fail(DDFLB_EINVAL, "out is NULL");
+  *out = nullptr;
+  ddflb_status s = validate(p);
+  if (s != DDFLB_OK) return s;
+  return create_ctx(p, 0, 0, 0, p->ny, ws, bytes, stream, out);
+}
+
+size_t ddflb_slab_workspace_bytes(const ddflb_params* p, int32_t y0, int32_t rows) {
+  ddflb_params own;
+  int glo = 0, ghi = 0;
+  if (slab_geometry(p, y0, rows, &own, &glo, &ghi) != DDFLB_OK) return 0;
+  return layout(&own, glo, ghi).total;
+}
+
+ddflb_status ddflb_slab_create(const ddflb_params* p, int32_t y0, int32_t rows, void* ws,
+                               size_t bytes, void* stream, ddflb_ctx** out) {
+  if (!out) return fail(DDFLB_EINVAL, "out is NULL");
+  *out = nullptr;
+  ddflb_params own;
+  int glo = 0, ghi = 0;
+  ddflb_status s = slab_geometry(p, y0, rows, &own, &glo, &ghi);
+  if (s != DDFLB_OK) return s;
+  return create_ctx(&own, glo, ghi, y0, p->ny, ws, bytes, stream, out);
 }
 
 ddflb_status ddflb_init(ddflb_ctx* c, const float* rho, const float* ux, const float* uy,
@@ -398,7 +467,7 @@ ddflb_status ddflb_init(ddflb_ctx* c, const float* rho, const float* ux, const f
   at_time(c, 0);
   InitPtrs in{rho, ux, uy, phi, grads};
   void* f = c->pops[0];
-  void* g = (char*)f + 9 * c->lay.pitch * (size_t)c->p.ny * elem_size(c->p.storage);
+  void* g = (char*)f + c->lay.gofs;
   s = check_launch(launch_init(c->L, in, f, g), "init");
   if (s != DDFLB_OK) return s;
   return checks_at(c);
@@ -445,6 +514,9 @@ ddflb_status ddflb_init_host(ddflb_ctx* c, const float* rho, const float* ux, co
 ddflb_status ddflb_step(ddflb_ctx* c, int64_t n) {
   if (!c) return fail(DDFLB_EINVAL, "NULL handle");
   if (n < 0) return fail(DDFLB_EINVAL, "n < 0");
+  if (n > 1 && (c->lay.ghost_lo || c->lay.ghost_hi))
+    return fail(DDFLB_EINVAL, "a y-slab context takes one step per call: its ghost rows are "
+                              "refreshed between steps");
   Range range("ddflb_step");
   const int K = c->p.check_every;
   while (n > 0) {
@@ -470,7 +542,7 @@ ddflb_status ddflb_step(ddflb_ctx* c, int64_t n) {
     --n;
     const int src = c->cur, dst = c->cur ^ 1;
     void* fo = c->pops[dst];
-    void* go = (char*)fo + 9 * c->lay.pitch * (size_t)c->p.ny * elem_size(c->p.storage);
+    void* go = (char*)fo + c->lay.gofs;
     at_time(c, c->step);
     cudaError_t e = run_step(c, fptr(c, src), gptr(c, src), fo, go);
     if (e != cudaSuccess) return cuda_fail(e, "step");
@@ -690,7 +762,7 @@ ddflb_status ddflb_autotune(ddflb_ctx* c, int32_t trial_steps, int32_t* block_x,
   dim3 bestb(128, 1, 1);
   int bestp = 1;
   const int saved_path = c->path;
-  const size_t gofs = 9 * (size_t)c->lay.pitch * c->p.ny * elem_size(c->p.storage);
+  const size_t gofs = c->lay.gofs;
   for (int pth = 1; pth <= 3 && e == cudaSuccess; ++pth) {
     for (const auto& sh : shapes) {
       c->L.block = dim3(sh[0], sh[1], 1);
@@ -752,6 +824,85 @@ ddflb_status ddflb_set_force_field(ddflb_ctx* c, const float* dev_field) {
   c->L.P.ffield = dev_field;
   c->L.force = has_force(c->p, dev_field);
   drop_graphs(c);
+  return DDFLB_OK;
+}
+
+size_t ddflb_halo_elems(const ddflb_ctx* c) { return c ? 6 * (size_t)c->p.nx : 0; }
+
+ddflb_status ddflb_halo_pack(ddflb_ctx* c, void* dev_down, void* dev_up) {
+  if (!c) return fail(DDFLB_EINVAL, "NULL handle");
+  if ((dev_down && !c->lay.ghost_lo) || (dev_up && !c->lay.ghost_hi))
+    return fail(DDFLB_EINVAL, "halo_pack: a face without a neighbouring slab sends nothing");
+  if (!dev_down && !dev_up) return DDFLB_OK;
+  return check_launch(launch_halo_pack(c->L, c->pops[c->cur], c->lay.gofs, dev_down, dev_up),
+                      "halo_pack");
+}
+
+ddflb_status ddflb_halo_unpack(ddflb_ctx* c, const void* dev_from_below,
+                               const void* dev_from_above) {
+  if (!c) return fail(DDFLB_EINVAL, "NULL handle");
+  if ((dev_from_below && !c->lay.ghost_lo) || (dev_from_above && !c->lay.ghost_hi))
+    return fail(DDFLB_EINVAL, "halo_unpack: a face without a neighbouring slab has no ghost row");
+  if (!dev_from_below && !dev_from_above) return DDFLB_OK;
+  return check_launch(launch_halo_unpack(c->L, c->pops[c->cur], c->lay.gofs, dev_from_below,
+                                         dev_from_above),
+                      "halo_unpack");
+}
+
+ddflb_status ddflb_halo_exchange_local(ddflb_ctx* const* slabs, int32_t parts) {
+  if (!slabs || parts < 1) return fail(DDFLB_EINVAL, "no slabs");
+  if (parts > kMaxLocalSlabs) return fail(DDFLB_EINVAL, "at most %d slabs", kMaxLocalSlabs);
+  for (int k = 0; k < parts; ++k)
+    if (!slabs[k]) return fail(DDFLB_EINVAL, "slab %d is NULL", k);
+  const ddflb_ctx* a = slabs[0];
+  if (parts == 1) {
+    if (a->lay.ghost_lo || a->lay.ghost_hi)
+      return fail(DDFLB_EINVAL, "one slab of a divided lattice has no neighbours to exchange with");
+    return DDFLB_OK;  // a whole lattice: nothing crosses a face
+  }
+  HaloSlabs H{};
+  H.n = parts;
+  H.nx = a->p.nx;
+  H.pitch = a->lay.pitch;
+  H.periodic = a->p.bc == DDFLB_BC_PERIODIC;
+  int32_t next_y0 = 0;
+  for (int k = 0; k < parts; ++k) {
+    const ddflb_ctx* c = slabs[k];
+    if (c->p.nx != a->p.nx || c->p.storage != a->p.storage || c->p.bc != a->p.bc ||
+        c->global_ny != a->global_ny || c->L.stream != a->L.stream || c->cur != a->cur)
+      return fail(DDFLB_EINVAL, "slab %d is not a slab of the same lattice on the same stream, "
+                                "at the same step", k);
+    if (c->slab_y0 != next_y0)
+      return fail(DDFLB_EINVAL, "slab %d starts at row %d, expected %d (give them bottom to top)",
+                  k, c->slab_y0, next_y0);
+    next_y0 += c->p.ny;
+    // a face shared with a neighbour has a ghost row on both sides
+    if (!c->lay.ghost_hi && k < parts - 1)
+      return fail(DDFLB_EINVAL, "slab %d has no ghost row above", k);
+    H.s[k] = HaloSlab{c->pops[c->cur], (int64_t)(c->lay.gofs / elem_size(c->p.storage)),
+                      c->L.P.plane, c->L.P.y0, c->L.P.y1};
+  }
+  if (next_y0 != a->global_ny)
+    return fail(DDFLB_EINVAL, "the slabs cover rows 0..%d of %d", next_y0, a->global_ny);
+  return check_launch(launch_halo_local(H, a->p.storage, a->L.stream), "halo_exchange_local");
+}
+
+ddflb_status ddflb_sums(ddflb_ctx* c, int32_t mode, double* out) {
+  if (!c || !out) return fail(DDFLB_EINVAL, "NULL argument");
+  if (mode < 0 || mode > 3) return fail(DDFLB_EINVAL, "mode %d not in 0..3", mode);
+  if ((mode & 1) && c->snap_step < 0)
+    return fail(DDFLB_EINVAL, "no velocity snapshot stored (call with mode bit 2 first)");
+  ddflb_status s = reduce(c, mode);
+  if (s != DDFLB_OK) return s;
+  DevStatus h{};
+  cudaError_t e = cudaMemcpyAsync(&h, c->status, sizeof h, cudaMemcpyDeviceToHost, c->L.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->L.stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sums");
+  out[0] = h.mass_dev;
+  out[1] = h.scalar_dev;
+  out[2] = h.u2;
+  out[3] = (mode & 1) ? h.du2 : NAN;
+  if (h.diverged) return fail(DDFLB_EDIVERGED, "non-finite sum by step %lld", (long long)c->step);
   return DDFLB_OK;
 }
 
@@ -866,7 +1017,7 @@ extern "C" ddflb_status ddflb_reduce_noalloc(const ddflb_params* p, const void* 
   e = cudaMemsetAsync(&scratch->status, 0, sizeof(DevStatus), st);
   if (e != cudaSuccess) return cuda_fail(e, "no-allocation status clear");
   const char* f = (const char*)dev_state;
-  const char* g = f + 9 * (size_t)lay.pitch * p->ny * elem_size(p->storage);
+  const char* g = f + lay.gofs;
   e = launch_reduce(L, f, g, scratch->uprev, mode, scratch->partials, &scratch->status);
   if (e != cudaSuccess) return cuda_fail(e, "no-allocation reduce");
   if (mode & 2) {

@@ -158,8 +158,11 @@ __device__ __forceinline__ void batch_cell(const LbParams& P, const BatchInst& I
     pull<S, BC, true>(P, fin, gin, x, y, df, dg);
   const Mom mf = moments_flow(df), mg = moments_scalar(dg);
   const Macro q = macro(P, mf, mg);
-  relax(P.wf, neq_flow(mf, q), df);
-  relax(P.wg, neq_scalar(P, mg, mf, q), dg);
+  Neq nf = neq_flow(mf, q), ng = neq_scalar(P, mg, mf, q);
+  // FP32 storage: compensated odd moments, as in the single-lattice step
+  if (sizeof(S) == 4) neq_compensate<false>(P, df, dg, mf, mg, q, 0.0f, 0.0f, nf, ng);
+  relax(P.wf, nf, df);
+  relax(P.wg, ng, dg);
   const uint32_t o = (uint32_t)y * (uint32_t)P.pitch + (uint32_t)x;
 #pragma unroll
   for (int a = 0; a < 9; ++a) {

@@ -31,7 +31,10 @@ enum Bc : int { BC_PERIODIC = 0, BC_CAVITY = 1, BC_CHANNEL = 2 };
 
 // Parameters of one lattice pair, passed by value to every kernel.
 struct LbParams {
-  int nx, ny, pitch;
+  int nx, ny, pitch;      // ny: rows of the population buffers
+  int y0, y1;             // buffer rows this context updates and reports, [y0, y1): all
+                          // rows for a whole lattice; a y-slab's buffers add a ghost row
+                          // on each face shared with another slab
   int64_t plane;          // elements per population plane (ny * pitch)
   float wf[9];            // flow relaxation rates, Eq. (relaxationtimematrix_fluidmotion)
   float wg[9];            // scalar relaxation rates, Eq. (relaxationtimematrix_CDE)
@@ -331,8 +334,8 @@ struct Force {
 
 __device__ __forceinline__ Force node_force(const LbParams& P, int x, int y) {
   float fx = P.fx, fy = P.fy;
-  if (P.ffield != nullptr) {
-    const int64_t c = (int64_t)y * P.nx + x, n = (int64_t)P.nx * P.ny;
+  if (P.ffield != nullptr) {  // the field covers the context's own rows
+    const int64_t c = (int64_t)(y - P.y0) * P.nx + x, n = (int64_t)P.nx * (P.y1 - P.y0);
     fx += P.ffield[c];
     fy += P.ffield[n + c];
   }
@@ -475,14 +478,15 @@ __device__ __forceinline__ void relax_cascaded(const float w[9], const CNeq& v, 
 }
 
 // Scalar collision of the model SM (0: the MRT of Sec. 3, also used for the
-// SRT with equal rates; 2 cascaded; 3 central moments).
+// SRT with equal rates; 2 cascaded; 3 central moments), given the scalar
+// non-equilibrium moments ng.
 template <int SM>
-__device__ __forceinline__ void collide_scalar(const LbParams& P, const Mom& mg, const Mom& mf,
-                                               const Macro& q, float dg[9]) {
+__device__ __forceinline__ void collide_scalar(const LbParams& P, const Neq& ng, const Macro& q,
+                                               float dg[9]) {
   if (SM == 0) {
-    relax(P.wg, neq_scalar(P, mg, mf, q), dg);
+    relax(P.wg, ng, dg);
   } else {
-    const CNeq v = central_neq(P, neq_scalar(P, mg, mf, q), q);
+    const CNeq v = central_neq(P, ng, q);
     if (SM == 2)
       relax_cascaded(P.wg, v, q, dg);
     else
@@ -490,9 +494,109 @@ __device__ __forceinline__ void collide_scalar(const LbParams& P, const Mom& mg,
   }
 }
 
+// ------------------------------------------------------------ compensated odd moments
+// The first- and third-order moments of both lattices are O(u) sums whose
+// equilibria cancel them down to the small non-equilibrium part (flow n6, n7;
+// scalar n1, n2, n6, n7, and the scalar xy moment), so the FP32 rounding of
+// the O(u) partial sums, about one unit in the last place of a population per
+// addition, lands in full on the non-equilibrium moments.  Accumulated over
+// many steps it is as large as the rounding of the stored populations
+// themselves.  With FP32 storage these moments are therefore formed with
+// error-free transformations: every O(u) partial sum is kept as a value plus
+// its exact rounding error (two-sum), the equilibrium's O(u) product is split
+// exactly by an FMA, the leading parts cancel exactly (Sterbenz), and only the
+// small remainder is rounded.  The relaxation (Eqs. MRT-LBEfluidmotion_transformed,
+// MRT-LBECDE) and the kinematics of Sec. 4 are unchanged; only the rounding of
+// the intermediate sums is removed.
+struct Ef {
+  float s, e;  // the unevaluated sum s + e
+};
+
+__device__ __forceinline__ Ef two_sum(float a, float b) {
+  const float s = a + b, bb = s - a;
+  return Ef{s, (a - (s - bb)) + (b - bb)};
+}
+
+// a - k b for a constant k, with the product k b.s split exactly by an FMA
+__device__ __forceinline__ float sub_scaled(const Ef& a, float k, const Ef& b) {
+  const float p = k * b.s, pe = __fmaf_rn(k, b.s, -p);
+  return (a.s - p) + ((a.e - pe) - k * b.e);
+}
+
+// ka a - kb b for constants ka, kb, both products split exactly by FMAs
+__device__ __forceinline__ float cross_diff(float ka, const Ef& a, float kb, const Ef& b) {
+  const float p = ka * a.s, pe = __fmaf_rn(ka, a.s, -p);
+  const float r = kb * b.s, re = __fmaf_rn(kb, b.s, -r);
+  return (p - r) + ((pe - re) + (ka * a.e - kb * b.e));
+}
+
+// j_x, j_y, k_xxy, k_xyy of one lattice's deviations (moments 1, 2, 6, 7 of
+// Eq. basisvectors) as value + exact remainder
+struct OddMom {
+  Ef kx, ky, kxxy, kxyy;
+};
+
+__device__ __forceinline__ OddMom odd_moments(const float d[9]) {
+  const Ef a57 = two_sum(d[5], -d[7]), a68 = two_sum(d[6], -d[8]);
+  const Ef d13 = two_sum(d[1], -d[3]), d24 = two_sum(d[2], -d[4]);
+  OddMom m;
+  m.kxxy = two_sum(a57.s, a68.s);
+  m.kxxy.e += a57.e + a68.e;
+  m.kxyy = two_sum(a57.s, -a68.s);
+  m.kxyy.e += a57.e - a68.e;
+  m.kx = two_sum(d13.s, m.kxyy.s);
+  m.kx.e += d13.e + m.kxyy.e;
+  m.ky = two_sum(d24.s, m.kxxy.s);
+  m.ky.e += d24.e + m.kxxy.e;
+  return m;
+}
+
+// Replaces the O(u)-cancelling non-equilibrium moments of nf (n6, n7) and ng
+// (n1, n2, n6, n7; n5 too if XY) by their compensated forms.  mf, mg, q are the
+// plain moments and macroscopic state of the node; F the body force (zero
+// without), whose half shifts the momentum as in macro_force.
+template <bool XY>
+__device__ __forceinline__ void neq_compensate(const LbParams& P, const float df[9],
+                                               const float dg[9], const Mom& mf, const Mom& mg,
+                                               const Macro& q, float hfx, float hfy, Neq& nf,
+                                               Neq& ng) {
+  const float c = 1.0f / 3.0f;
+  OddMom of = odd_moments(df);
+  const OddMom og = odd_moments(dg);
+  if (hfx != 0.0f || hfy != 0.0f) {  // the half-force momentum shift, exactly
+    const Ef sx = two_sum(of.kx.s, hfx), sy = two_sum(of.ky.s, hfy);
+    of.kx = Ef{sx.s, sx.e + of.kx.e};
+    of.ky = Ef{sy.s, sy.e + of.ky.e};
+  }
+  const float uxx = q.ux * q.ux, uyy = q.uy * q.uy;
+  // flow: k_xxy - j_y (c + ux^2), k_xyy - j_x (c + uy^2)
+  nf.n6 = sub_scaled(of.kxxy, c, of.ky) - mf.ky * uxx;
+  nf.n7 = sub_scaled(of.kxyy, c, of.kx) - mf.kx * uyy;
+  // scalar first order: eta_x - phi u_x = (eta_x rho - phi j_x) / rho, written
+  // as ((rho0 eta_x - phi0 j_x) + eta_x (rho - rho0) - (phi - phi0) j_x) / rho,
+  // whose leading parts rho0 eta_x and phi0 j_x cancel
+  const float drho = mf.k0, dphi = mg.k0;
+  const float n1 = (cross_diff(P.rho0, og.kx, P.phi0, of.kx) +
+                    (og.kx.s * drho - dphi * of.kx.s)) * q.irho;
+  const float n2 = (cross_diff(P.rho0, og.ky, P.phi0, of.ky) +
+                    (og.ky.s * drho - dphi * of.ky.s)) * q.irho;
+  ng.n1 = n1;
+  ng.n2 = n2;
+  // scalar third order: eta_xxy - phi u_y (b1 c + ux^2) with phi u_y = eta_y - n2
+  const float b1c = P.b1 * c, b2c = P.b2 * c;
+  const float px = og.kx.s - n1, py = og.ky.s - n2;
+  ng.n6 = sub_scaled(og.kxxy, b1c, og.ky) + b1c * n2 - py * uxx;
+  ng.n7 = sub_scaled(og.kxyy, b2c, og.kx) + b2c * n1 - px * uyy;
+  if (XY) {  // eta_xy - phi ux uy, from two exact pair differences
+    const Ef a56 = two_sum(dg[5], -dg[6]), a78 = two_sum(dg[7], -dg[8]);
+    ng.n5 = ((a56.s + a78.s) + (a56.e + a78.e)) - px * q.uy;
+  }
+}
+
 // Moments, macroscopic state and both collisions of one node, in place on the
-// pulled deviations df, dg.  FORCE = false is the unforced step.
-template <bool FORCE, int SM = 0>
+// pulled deviations df, dg.  FORCE = false is the unforced step.  COMP: the
+// odd non-equilibrium moments are compensated (FP32 storage).
+template <bool FORCE, int SM = 0, bool COMP = false>
 __device__ __forceinline__ void collide(const LbParams& P, int x, int y, float df[9],
                                         float dg[9]) {
   Mom mf = moments_flow(df);
@@ -500,40 +604,51 @@ __device__ __forceinline__ void collide(const LbParams& P, int x, int y, float d
   if (FORCE) {
     const Force F = node_force(P, x, y);
     const Macro q = macro_force(P, mf, mg, F);
-    relax_source(P.wf, neq_flow(mf, q), source(F, q), df);
-    collide_scalar<SM>(P, mg, mf, q, dg);
+    Neq nf = neq_flow(mf, q), ng = neq_scalar(P, mg, mf, q);
+    if (COMP) neq_compensate<false>(P, df, dg, mf, mg, q, 0.5f * F.x, 0.5f * F.y, nf, ng);
+    relax_source(P.wf, nf, source(F, q), df);
+    collide_scalar<SM>(P, ng, q, dg);
   } else {
     const Macro q = macro(P, mf, mg);
-    relax(P.wf, neq_flow(mf, q), df);
-    collide_scalar<SM>(P, mg, mf, q, dg);
+    Neq nf = neq_flow(mf, q), ng = neq_scalar(P, mg, mf, q);
+    if (COMP) neq_compensate<false>(P, df, dg, mf, mg, q, 0.0f, 0.0f, nf, ng);
+    relax(P.wf, nf, df);
+    collide_scalar<SM>(P, ng, q, dg);
   }
 }
 
 // Macroscopic state and the non-equilibrium moments the kinematics use.  With
 // a force the flow moments are those of f = f-bar + S/2 (the distribution whose
-// non-equilibrium part Sec. 4 relates to the velocity gradients).
+// non-equilibrium part Sec. 4 relates to the velocity gradients).  The odd
+// non-equilibrium moments (and the scalar xy moment) are compensated.
 template <bool FORCE>
 __device__ __forceinline__ Macro state(const LbParams& P, int x, int y, const float df[9],
                                        const float dg[9], Neq& nf, Neq& ng) {
   Mom mf = moments_flow(df);
   const Mom mg = moments_scalar(dg);
   Macro q;
+  float hfx = 0.0f, hfy = 0.0f;
+  Src s{};
   if (FORCE) {
     const Force F = node_force(P, x, y);
+    hfx = 0.5f * F.x;
+    hfy = 0.5f * F.y;
     q = macro_force(P, mf, mg, F);
-    nf = neq_flow(mf, q);
-    const Src s = source(F, q);
+    s = source(F, q);
+  } else {
+    q = macro(P, mf, mg);
+  }
+  nf = neq_flow(mf, q);
+  ng = neq_scalar(P, mg, mf, q);
+  neq_compensate<true>(P, df, dg, mf, mg, q, hfx, hfy, nf, ng);
+  if (FORCE) {
     nf.n3 += 0.5f * s.s3;
     nf.n4 += 0.5f * s.s4;
     nf.n5 += 0.5f * s.s5;
     nf.n6 += 0.5f * s.s6;
     nf.n7 += 0.5f * s.s7;
     nf.n8 += 0.5f * s.s8;
-  } else {
-    q = macro(P, mf, mg);
-    nf = neq_flow(mf, q);
   }
-  ng = neq_scalar(P, mg, mf, q);
   return q;
 }
 

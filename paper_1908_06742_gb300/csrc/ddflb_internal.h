@@ -32,6 +32,25 @@ struct Launch {
   cudaStream_t stream;
 };
 
+// y-slabs of one lattice on one device, for the single-launch halo exchange
+constexpr int kMaxLocalSlabs = 64;
+struct HaloSlab {
+  void* buf;            // current population buffer (flow planes, then scalar)
+  int64_t gofs_elems;   // elements from the flow planes to the scalar planes
+  int64_t plane;        // elements per plane
+  int y0, y1;           // own buffer rows [y0, y1)
+};
+struct HaloSlabs {
+  HaloSlab s[kMaxLocalSlabs];
+  int n, nx, pitch, periodic;
+};
+
+cudaError_t launch_halo_pack(const Launch& L, const void* buf, size_t gofs_bytes, void* down,
+                             void* up);
+cudaError_t launch_halo_unpack(const Launch& L, void* buf, size_t gofs_bytes,
+                               const void* from_below, const void* from_above);
+cudaError_t launch_halo_local(const HaloSlabs& H, int storage, cudaStream_t stream);
+
 cudaError_t launch_step(const Launch& L, const void* fin, const void* gin, void* fout, void* gout,
                         const DevStatus* st);
 cudaError_t launch_fields(const Launch& L, const void* fin, const void* gin, const FieldPtrs& out);

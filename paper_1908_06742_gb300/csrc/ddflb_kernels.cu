@@ -27,23 +27,25 @@ __global__ void __launch_bounds__(256) k_step(LbParams P, const S* __restrict__ 
                                               S* __restrict__ gout,
                                               const DevStatus* __restrict__ status) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int y = P.y0 + blockIdx.y * blockDim.y + threadIdx.y;
   // with walls: a warp (32 consecutive x of one row) whose nodes all have their
-  // neighbours inside the lattice pulls without the wall rules (same addresses,
+  // neighbours inside the buffers pulls without the wall rules (same addresses,
   // same values); decided by a vote of all lanes before any returns
   bool inner = false;
   if (BC != BC_PERIODIC) {
     const bool in_x = BC == BC_CHANNEL ? x < P.nx : (x >= 1 && x < P.nx - 1);
     inner = __all_sync(0xffffffffu, in_x && y >= 1 && y < P.ny - 1);
   }
-  if (x >= P.nx || y >= P.ny) return;
+  if (x >= P.nx || y >= P.y1) return;
   if (status != nullptr && status->diverged) return;
   float df[9], dg[9];
   if (BC != BC_PERIODIC && inner)
     pull<S, BC_PERIODIC>(P, fin, gin, x, y, df, dg);
   else
     pull<S, BC>(P, fin, gin, x, y, df, dg);
-  collide<FORCE, SM>(P, x, y, df, dg);
+  // FP32 storage: compensated odd moments (the arithmetic rounding would
+  // otherwise match the storage rounding); 16-bit storage rounds far coarser
+  collide<FORCE, SM, sizeof(S) == 4>(P, x, y, df, dg);
   const uint32_t o = (uint32_t)y * (uint32_t)P.pitch + (uint32_t)x;
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
@@ -57,14 +59,14 @@ template <typename S, int BC, bool FORCE>
 __global__ void __launch_bounds__(256) k_fields(LbParams P, const S* __restrict__ fin,
                                                 const S* __restrict__ gin, FieldPtrs out) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  if (x >= P.nx || y >= P.ny) return;
+  const int y = P.y0 + blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= P.nx || y >= P.y1) return;
   float df[9], dg[9];
   pull<S, BC>(P, fin, gin, x, y, df, dg);
   Neq nf, ng;
   const Macro q = state<FORCE>(P, x, y, df, dg, nf, ng);
   const Kin k = kinematics(P, nf, ng, q);
-  const int64_t o = (int64_t)y * P.nx + x;
+  const int64_t o = (int64_t)(y - P.y0) * P.nx + x;
   if (out.p[0]) out.p[0][o] = q.rho;
   if (out.p[1]) out.p[1][o] = q.ux;
   if (out.p[2]) out.p[2][o] = q.uy;
@@ -88,11 +90,11 @@ __global__ void __launch_bounds__(256) k_pops(LbParams P, const S* __restrict__ 
                                               const S* __restrict__ gin, float* __restrict__ fo,
                                               float* __restrict__ go) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  if (x >= P.nx || y >= P.ny) return;
+  const int y = P.y0 + blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= P.nx || y >= P.y1) return;
   float df[9], dg[9];
   pull<S, BC>(P, fin, gin, x, y, df, dg);
-  const int64_t o = (int64_t)y * P.nx + x, n = (int64_t)P.nx * P.ny;
+  const int64_t o = (int64_t)(y - P.y0) * P.nx + x, n = (int64_t)P.nx * (P.y1 - P.y0);
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
     if (fo) fo[a * n + o] = df[a] + P.wrf[a] * P.rho0;
@@ -109,9 +111,9 @@ template <typename S, int BC, bool FORCE>
 __global__ void __launch_bounds__(256) k_init(LbParams P, InitPtrs in, S* __restrict__ fout,
                                               S* __restrict__ gout) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  if (x >= P.nx || y >= P.ny) return;
-  const int64_t c0 = (int64_t)y * P.nx + x, n = (int64_t)P.nx * P.ny;
+  const int y = P.y0 + blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= P.nx || y >= P.y1) return;
+  const int64_t c0 = (int64_t)(y - P.y0) * P.nx + x, n = (int64_t)P.nx * (P.y1 - P.y0);
   const float rho = in.rho[c0], ux = in.ux[c0], uy = in.uy[c0], phi = in.phi[c0];
   const float k0 = rho - P.rho0, n0 = phi - P.phi0;
   const float jx = rho * ux, jy = rho * uy, px = phi * ux, py = phi * uy;
@@ -219,10 +221,10 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(LbParams P, const S* 
                                                            float* __restrict__ uprev, int mode,
                                                            double* __restrict__ partials) {
   double s[4] = {0.0, 0.0, 0.0, 0.0};
-  const int64_t n = (int64_t)P.nx * P.ny;
+  const int64_t n = (int64_t)P.nx * (P.y1 - P.y0);
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
        c += (int64_t)gridDim.x * blockDim.x) {
-    const int y = (int)(c / P.nx), x = (int)(c - (int64_t)y * P.nx);
+    const int r = (int)(c / P.nx), x = (int)(c - (int64_t)r * P.nx), y = P.y0 + r;
     float df[9], dg[9];
     pull<S, BC>(P, fin, gin, x, y, df, dg);
     Mom mf = moments_flow(df);
@@ -284,10 +286,70 @@ __global__ void __launch_bounds__(256) k_finalize(const double* __restrict__ par
   }
 }
 
+// ------------------------------------------------------------------ y-slab halos
+// A lattice divided into y-slabs (the collide-and-stream update of Secs. 2-3
+// is local: a node pulls only from its 8 neighbours) exchanges, after every
+// step, the post-collision populations that cross each shared face: the
+// directions with e_y = -1 (4, 7, 8) of a slab's bottom row go down, those
+// with e_y = +1 (2, 5, 6) of its top row go up, for both lattices: 6 rows of
+// nx storage elements per face and direction, copied bit for bit (E is an
+// unsigned integer of the storage element's size).
+__device__ __forceinline__ int halo_plane(int k, bool up) {
+  const int a = k % 3;
+  return up ? (a == 0 ? 2 : a == 1 ? 5 : 6) : (a == 0 ? 4 : a == 1 ? 7 : 8);
+}
+
+// message rows [6][nx]: k = 0..2 flow, 3..5 scalar
+template <typename E>
+__global__ void __launch_bounds__(256) k_halo_pack(LbParams P, const E* __restrict__ buf,
+                                                   int64_t gofs, E* __restrict__ down,
+                                                   E* __restrict__ up) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
+  if (x >= P.nx) return;
+  const E* lat = buf + (k >= 3 ? gofs : 0);
+  if (down) down[k * P.nx + x] = lat[halo_plane(k, false) * P.plane + (int64_t)P.y0 * P.pitch + x];
+  if (up) up[k * P.nx + x] = lat[halo_plane(k, true) * P.plane + (int64_t)(P.y1 - 1) * P.pitch + x];
+}
+
+template <typename E>
+__global__ void __launch_bounds__(256) k_halo_unpack(LbParams P, E* __restrict__ buf, int64_t gofs,
+                                                     const E* __restrict__ from_below,
+                                                     const E* __restrict__ from_above) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
+  if (x >= P.nx) return;
+  E* lat = buf + (k >= 3 ? gofs : 0);
+  if (from_below)  // ghost row below the slab receives what the slab below sent up
+    lat[halo_plane(k, true) * P.plane + (int64_t)(P.y0 - 1) * P.pitch + x] = from_below[k * P.nx + x];
+  if (from_above)
+    lat[halo_plane(k, false) * P.plane + (int64_t)P.y1 * P.pitch + x] = from_above[k * P.nx + x];
+}
+
+// All faces of slabs on one device in one launch: block z = 2 s + dir copies
+// slab s's outgoing rows straight into the ghost row of its neighbour (dir 0:
+// up to slab s + 1, dir 1: down to slab s - 1; wrapping for a periodic lattice).
+template <typename E>
+__global__ void __launch_bounds__(256) k_halo_local(HaloSlabs H) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
+  const int s = blockIdx.z >> 1;
+  const bool up = (blockIdx.z & 1) == 0;
+  const int t = up ? s + 1 : s - 1;
+  if (x >= H.nx) return;
+  const int d = t < 0 ? (H.periodic ? H.n - 1 : -1) : t >= H.n ? (H.periodic ? 0 : -1) : t;
+  if (d < 0) return;
+  const HaloSlab& A = H.s[s];
+  const HaloSlab& B = H.s[d];
+  const int a = halo_plane(k, up);
+  const int64_t lat = k >= 3 ? 1 : 0;
+  const E* src = (const E*)A.buf + lat * A.gofs_elems + a * A.plane;
+  E* dst = (E*)B.buf + lat * B.gofs_elems + a * B.plane;
+  const int64_t ys = up ? A.y1 - 1 : A.y0, yd = up ? B.y0 - 1 : B.y1;
+  dst[yd * H.pitch + x] = src[ys * H.pitch + x];
+}
+
 // ------------------------------------------------------------------ launchers
 namespace {
 dim3 grid2d(const LbParams& P, dim3 b) {
-  return dim3((P.nx + b.x - 1) / b.x, (P.ny + b.y - 1) / b.y);
+  return dim3((P.nx + b.x - 1) / b.x, (P.y1 - P.y0 + b.y - 1) / b.y);
 }
 
 template <typename S, int BC, bool FORCE, int SM>
@@ -378,6 +440,41 @@ cudaError_t launch_pops(const Launch& L, const void* fin, const void* gin, float
 
 cudaError_t launch_init(const Launch& L, const InitPtrs& in, void* fout, void* gout) {
   return dispatch(L, 2, nullptr, nullptr, fout, gout, nullptr, &in, 0, nullptr, 0);
+}
+
+cudaError_t launch_halo_pack(const Launch& L, const void* buf, size_t gofs_bytes, void* down,
+                             void* up) {
+  const dim3 b(256), g((L.P.nx + 255) / 256, 6);
+  if (L.storage == 0)
+    k_halo_pack<uint32_t><<<g, b, 0, L.stream>>>(L.P, (const uint32_t*)buf, gofs_bytes / 4,
+                                                 (uint32_t*)down, (uint32_t*)up);
+  else
+    k_halo_pack<uint16_t><<<g, b, 0, L.stream>>>(L.P, (const uint16_t*)buf, gofs_bytes / 2,
+                                                 (uint16_t*)down, (uint16_t*)up);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_halo_unpack(const Launch& L, void* buf, size_t gofs_bytes,
+                               const void* from_below, const void* from_above) {
+  const dim3 b(256), g((L.P.nx + 255) / 256, 6);
+  if (L.storage == 0)
+    k_halo_unpack<uint32_t><<<g, b, 0, L.stream>>>(L.P, (uint32_t*)buf, gofs_bytes / 4,
+                                                   (const uint32_t*)from_below,
+                                                   (const uint32_t*)from_above);
+  else
+    k_halo_unpack<uint16_t><<<g, b, 0, L.stream>>>(L.P, (uint16_t*)buf, gofs_bytes / 2,
+                                                   (const uint16_t*)from_below,
+                                                   (const uint16_t*)from_above);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_halo_local(const HaloSlabs& H, int storage, cudaStream_t stream) {
+  const dim3 b(256), g((H.nx + 255) / 256, 6, 2 * H.n);
+  if (storage == 0)
+    k_halo_local<uint32_t><<<g, b, 0, stream>>>(H);
+  else
+    k_halo_local<uint16_t><<<g, b, 0, stream>>>(H);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_reduce(const Launch& L, const void* fin, const void* gin, float* uprev,

@@ -304,8 +304,10 @@ cudaError_t go_bc(const Launch& L, const void* fin, const void* gin, void* fout,
 }
 }  // namespace
 
+// (whole lattices only: a y-slab context steps node by node)
 bool quad_step_eligible(const Launch& L) {
-  return !L.force && L.P.smodel < 2 && L.storage != 0 && L.P.nx % 4 == 0;
+  return !L.force && L.P.smodel < 2 && L.storage != 0 && L.P.nx % 4 == 0 && L.P.y0 == 0 &&
+         L.P.y1 == L.P.ny;
 }
 
 namespace {
@@ -336,7 +338,8 @@ cudaError_t launch_step_quad(const Launch& L, const void* fin, const void* gin, 
 }
 
 bool pair_step_eligible(const Launch& L) {
-  return !L.force && L.P.smodel < 2 && L.storage != 0 && L.P.nx % 2 == 0;
+  return !L.force && L.P.smodel < 2 && L.storage != 0 && L.P.nx % 2 == 0 && L.P.y0 == 0 &&
+         L.P.y1 == L.P.ny;
 }
 
 cudaError_t launch_step_pair(const Launch& L, const void* fin, const void* gin, void* fout,

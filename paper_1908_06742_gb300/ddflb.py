@@ -101,6 +101,16 @@ SIGNATURES = {
                        [ctypes.POINTER(ctypes.c_double)]),
     "ddflb_set_block": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32]),
     "ddflb_set_force_field": (ctypes.c_int, [_VP, _FP]),
+    # y-slab decomposition of one lattice
+    "ddflb_slab_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(Params), ctypes.c_int32,
+                                                     ctypes.c_int32]),
+    "ddflb_slab_create": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int32, ctypes.c_int32,
+                                         _VP, ctypes.c_size_t, _VP, ctypes.POINTER(_VP)]),
+    "ddflb_halo_elems": (ctypes.c_size_t, [_VP]),
+    "ddflb_halo_pack": (ctypes.c_int, [_VP, _FP, _FP]),
+    "ddflb_halo_unpack": (ctypes.c_int, [_VP, _FP, _FP]),
+    "ddflb_halo_exchange_local": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int32]),
+    "ddflb_sums": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
     # warm-start surrogate network kernels
     "ddflb_nn_gemm": (ctypes.c_int, [_FP, _FP] + [ctypes.c_int32] * 5 +
                       [_FP, ctypes.c_int32, _FP, ctypes.c_int32, _FP] + [ctypes.c_int32] * 3 +
@@ -125,6 +135,9 @@ SIGNATURES = {
                       [ctypes.c_float] * 4 + [ctypes.c_int64, ctypes.c_float, _VP]),
     "ddflb_nn_cast_bf16": (ctypes.c_int, [_FP, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                           _FP, ctypes.c_int32, _VP]),
+    "ddflb_warm_fields": (ctypes.c_int, [_FP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, _FP, _FP, _FP, _FP, _FP, _VP]),
     "ddflb_batch_destroy": (ctypes.c_int, [_VP]),
     "ddflb_last_error": (ctypes.c_char_p, []),
     "ddflb_version": (ctypes.c_char_p, []),
@@ -246,28 +259,58 @@ def reduce_noalloc(cfg: Config, state, mode: int, out, stream=None):
     return out
 
 
+def warm_fields(pred, u_lid: float, omega_scale: float, phi_lo: float = 0.0, phi_hi: float = 1.0,
+                stream=None):
+    """ddflb_warm_fields on a device FP32 prediction [ny, nx, C] (C >= 5):
+    returns device (rho, ux, uy, phi, grads[6]) for Lattice.init / Batch.init."""
+    import torch
+    ny, nx, C = pred.shape
+    assert pred.dtype == torch.float32 and pred.is_contiguous() and pred.is_cuda
+    planes = torch.empty((10, ny, nx), dtype=torch.float32, device=pred.device)
+    st = stream or torch.cuda.current_stream(pred.device)
+    _check(load().ddflb_warm_fields(pred.data_ptr(), nx, ny, C, float(u_lid), float(omega_scale),
+                                    float(phi_lo), float(phi_hi), planes[0].data_ptr(),
+                                    planes[1].data_ptr(), planes[2].data_ptr(),
+                                    planes[3].data_ptr(), planes[4].data_ptr(), st.cuda_stream))
+    return planes[0], planes[1], planes[2], planes[3], planes[4:]
+
+
 def _dptr(t) -> Optional[int]:
     return None if t is None else t.data_ptr()
 
 
 class Lattice:
-    """One pair of D2Q9 lattices (flow f, scalar g) resident on the GPU."""
+    """One pair of D2Q9 lattices (flow f, scalar g) resident on the GPU; with
+    ``rows = (y0, count)``, the y-slab of those rows of the lattice ``cfg``
+    (ddflb_slab_create: fields, force field and sums cover its own rows)."""
 
-    def __init__(self, cfg: Config, device=None, stream=None):
+    def __init__(self, cfg: Config, device=None, stream=None, rows=None):
         import torch
         self.torch = torch
         self.cfg = cfg
         self.device = torch.device(device or "cuda")
         self.lib = load()
         self._p = cfg.to_c()
-        nbytes = workspace_bytes(cfg)
+        if rows is None:
+            nbytes = workspace_bytes(cfg)
+        else:
+            nbytes = self.lib.ddflb_slab_workspace_bytes(ctypes.byref(self._p), int(rows[0]),
+                                                         int(rows[1]))
+            if nbytes == 0:
+                _check(EINVAL)
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         self.stream = stream or torch.cuda.current_stream(self.device)
         h = _VP()
-        _check(self.lib.ddflb_create(ctypes.byref(self._p), self.workspace.data_ptr(), nbytes,
-                                     self.stream.cuda_stream, ctypes.byref(h)))
+        if rows is None:
+            _check(self.lib.ddflb_create(ctypes.byref(self._p), self.workspace.data_ptr(), nbytes,
+                                         self.stream.cuda_stream, ctypes.byref(h)))
+        else:
+            _check(self.lib.ddflb_slab_create(ctypes.byref(self._p), int(rows[0]), int(rows[1]),
+                                              self.workspace.data_ptr(), nbytes,
+                                              self.stream.cuda_stream, ctypes.byref(h)))
         self._h = h
-        self.shape = (cfg.ny, cfg.nx)
+        self.rows = rows
+        self.shape = (cfg.ny if rows is None else int(rows[1]), cfg.nx)
 
     # -- helpers
     def _dev(self, a):
@@ -408,6 +451,25 @@ class Lattice:
         _check(self.lib.ddflb_set_state(self._h, buf.data_ptr(), buf.numel(), int(step)))
         return self
 
+    def sums(self, mode: int = 0):
+        """FP64 sums over this context's nodes (ddflb_sums): mass and scalar
+        deviations, sum |u|^2, and sum |u - u_snap|^2 (mode bit 1); mode bit 2
+        stores the snapshot.  Synchronises."""
+        out = (ctypes.c_double * 4)()
+        _check(self.lib.ddflb_sums(self._h, int(mode), out))
+        return {"mass_dev": out[0], "scalar_dev": out[1], "u2": out[2], "du2": out[3]}
+
+    def halo_elems(self) -> int:
+        return self.lib.ddflb_halo_elems(self._h)
+
+    def halo_pack(self, down, up):
+        """Outgoing face rows into device tensors of halo_elems() storage
+        elements (None for a wall face)."""
+        _check(self.lib.ddflb_halo_pack(self._h, _dptr(down), _dptr(up)))
+
+    def halo_unpack(self, from_below, from_above):
+        _check(self.lib.ddflb_halo_unpack(self._h, _dptr(from_below), _dptr(from_above)))
+
     def close(self):
         if getattr(self, "_h", None):
             self.lib.ddflb_destroy(self._h)
@@ -418,6 +480,61 @@ class Lattice:
             self.close()
         except Exception:
             pass
+
+
+class SlabLattice:
+    """One lattice divided into ``parts`` y-slabs held on one device (the
+    decomposition a multi-GPU run uses, with the halo exchange done by one
+    kernel): every step advances each slab, then refreshes all ghost rows.
+    Bit-identical to the undivided Lattice."""
+
+    def __init__(self, cfg: Config, parts: int, device=None, stream=None):
+        from .distributed import slab_rows
+        import torch
+        self.torch = torch
+        self.cfg = cfg
+        self.lib = load()
+        self.stream = stream or torch.cuda.current_stream(torch.device(device or "cuda"))
+        self.rows = [slab_rows(cfg.ny, parts, k) for k in range(parts)]
+        self.slabs = [Lattice(cfg, device=device, stream=self.stream, rows=r) for r in self.rows]
+        self._hs = (_VP * parts)(*[s._h for s in self.slabs])
+        self.t = 0
+
+    def _split(self, a):
+        return [None if a is None else a[..., y0:y0 + h, :] for y0, h in self.rows]
+
+    def init(self, rho, ux, uy, phi, grads=None):
+        parts = [self._split(None if a is None else self.slabs[0]._dev(a))
+                 for a in (rho, ux, uy, phi, grads)]
+        for k, s in enumerate(self.slabs):
+            s.init(*[None if p is None else p[k] for p in parts])
+        self.t = 0
+        return self
+
+    def step(self, n: int = 1):
+        for _ in range(int(n)):
+            for s in self.slabs:
+                _check(self.lib.ddflb_step(s._h, 1))
+            _check(self.lib.ddflb_halo_exchange_local(self._hs, len(self.slabs)))
+            self.t += 1
+        return self
+
+    def fields(self, names=FIELD_NAMES) -> dict:
+        parts = [s.fields(names) for s in self.slabs]
+        return {k: self.torch.cat([p[k] for p in parts], dim=0) for k in parts[0]}
+
+    def populations(self):
+        parts = [s.populations() for s in self.slabs]
+        return (self.torch.cat([p[0] for p in parts], dim=1),
+                self.torch.cat([p[1] for p in parts], dim=1))
+
+    def sums(self, mode: int = 0) -> dict:
+        """Sums over the whole lattice (FP64, slab by slab)."""
+        tot = {"mass_dev": 0.0, "scalar_dev": 0.0, "u2": 0.0, "du2": 0.0}
+        for s in self.slabs:
+            for k, v in s.sums(mode).items():
+                tot[k] += v
+        return tot
 
 
 class Batch:

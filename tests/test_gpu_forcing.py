@@ -2,8 +2,9 @@
 f - S/2, u = (sum f-bar e + F/2)/rho) with the FP64 oracle, on the paper's
 forced validation flows (Secs. 5.1-5.3) and on random states element by
 element.  Bounds as in the unforced parity tests: 1e-5 relative L2 on u, phi
-and S for FP32 storage; omega within three times the emulated FP32-storage
-floor (the oracle run with every stored population rounded to FP32)."""
+and S for FP32 storage, or 1.2 times the emulated FP32-storage floor (the
+oracle run with every stored population rounded to FP32) where that floor
+itself lies above 1e-5; omega within three times the emulated floor."""
 import math
 
 import numpy as np
@@ -55,11 +56,17 @@ def emulated_fields(s, F, steps, use_grads=False, force=None):
 
 
 def check(e, floor, target=1e-5):
+    """u, phi, S within the target, or within 1.2 times the emulated storage
+    floor where the floor is above the target: the long forced channel run
+    (30000 steps of a steady force) rounds the stored momentum the same way
+    every step, and FP32 storage alone leaves u at 1.35e-5 there; the kernel's
+    compensated arithmetic lands on that floor (1.31e-5).  omega within three
+    times the floor."""
     for k, v in e.items():
         if k == "omega":
             assert v <= max(target, 3 * floor[k]), (k, v, floor[k])
         else:
-            assert v <= target, (k, v, target)
+            assert v <= max(target, 1.2 * floor[k]), (k, v, target, floor[k])
 
 
 # --------------------------------------------------------------- element by element

@@ -69,9 +69,11 @@ def check(e, floor, target, exempt=()):
 # --------------------------------------------------------------- Taylor-Green
 def test_taylor_green_c1_fp32():
     """64^2 decaying Taylor-Green, U0 = 0.01, nu = D = 0.01, other rates 1.2,
-    phi = 1 + 0.1 sin sin, 1000 steps: u, phi, S within 1e-5 of FP64; omega,
-    which amplifies storage rounding by ~1/(beta1 - beta2), within three times
-    the FP32-storage floor (emulated 7.7e-6)."""
+    phi = 1 + 0.1 sin sin, 1000 steps: u, phi, S and omega all within 1e-5 of
+    FP64, with no exemption.  omega amplifies population rounding by about
+    2 / (beta1 - beta2); the FP32-storage floor alone (oracle emulation) is
+    7.6e-6, and the compensated odd moments keep the kernel's own arithmetic
+    from adding much to it (plain FP32 arithmetic gave 1.4e-5)."""
     s = spec(64, 64, nu=0.01)
     F = inputs.taylor_green(64, 0.01, phi_amp=0.1)
     g, o = run_both(s, F, 1000)
@@ -79,7 +81,7 @@ def test_taylor_green_c1_fp32():
     e = errors({k: np64(v) for k, v in g.fields().items()}, fo)
     floor = errors(emulated(s, F, 1000).fields(), fo)
     print("C1 fp32 errors", e, "emulated FP32-storage floor", floor)
-    check(e, floor, 1e-5, exempt=("omega",))
+    check(e, floor, 1e-5)
 
 
 @pytest.mark.parametrize("bc", ["periodic", "cavity", "channel"])
@@ -375,12 +377,13 @@ def test_sweep_size_1024_errors(storage, scale):
     200 steps, the sweep's launch configuration: one node per thread at FP32,
     four nodes per thread at 16 bit, FP16 scale 2^10): relative-L2 errors of u,
     phi, S and omega against the FP64 oracle.  FP32: u and phi within 1e-5; S
-    and omega within 1e-5 or three times the error of the oracle's own
-    FP32-storage emulation (at this size storage rounding alone gives S 7.5e-6
-    and omega 1.8e-4: the velocity gradients are U0 k = 6e-5).  16 bit: every
-    field within three times the emulation of the same storage and scale; at
-    FP16 u and phi also within 2e-3.  Measured: FP32 u 8.1e-8, phi 2.8e-8,
-    S 1.17e-5, omega 3.2e-4; FP16 u 8.4e-4, phi 2.5e-4, S 6.2e-2, omega 1.45;
+    and omega within 1.2 times the error of the oracle's own FP32-storage
+    emulation (at this size storage rounding alone gives S 7.5e-6 and omega
+    1.8e-4: the velocity gradients are U0 k = 6e-5), so the compensated
+    arithmetic may add at most a fifth to the storage floor (plain FP32
+    arithmetic gave 1.57 and 1.78 times it).  16 bit: every field within three
+    times the emulation of the same storage and scale; at FP16 u and phi also
+    within 2e-3.  Measured: FP16 u 8.4e-4, phi 2.5e-4, S 6.2e-2, omega 1.45;
     BF16 u 4.7e-3, phi 4.7e-4, S 0.49, omega 11 (each on its emulated floor)."""
     n, steps = 1024, 200
     s = spec(n, n, storage=storage, scale=scale)
@@ -398,7 +401,7 @@ def test_sweep_size_1024_errors(storage, scale):
           "emulation", {k: f"{v:.2e}" for k, v in floor.items()})
     for k, v in e.items():
         if storage == "fp32":
-            bound = max(1e-5, 3 * floor[k]) if k in ("omega", "S") else 1e-5
+            bound = 1.2 * floor[k] if k in ("omega", "S") else 1e-5
         else:
             bound = 3 * floor[k] + 1e-7
         assert v <= bound, (k, v, floor[k])
@@ -471,4 +474,4 @@ def test_full_size_sampled_windows(storage, scale):
             err = np.sqrt(np.mean((got - ref[k][win, win]) ** 2))
             floor = np.sqrt(np.mean((emu[k][win, win] - ref[k][win, win]) ** 2))
             print(storage, k, (cx, cy), "err", err, "emulation floor", floor)
-            assert err <= 5 * floor + 1e-5 * scale[k], (k, cx, cy, err, floor)
+            assert err <= 3 * floor + 1e-5 * scale[k], (k, cx, cy, err, floor)
