@@ -387,6 +387,7 @@ ddflb_status ddflb_sums(ddflb_ctx* c, int32_t mode, double* out);
  * whose sums are not finite (diverged) is frozen from then on. */
 #define DDFLB_INST_CONVERGED 1
 #define DDFLB_INST_DIVERGED 2
+#define DDFLB_INST_CAPPED 4  /* frozen at its own step limit without converging */
 typedef struct ddflb_batch ddflb_batch;
 
 /* Workspace bytes for n instances with parameters p[0..n-1] (0 if invalid). */
@@ -402,6 +403,25 @@ ddflb_status ddflb_batch_create(int32_t n, const ddflb_params* p, void* dev_work
  * to fall below tol (the vorticity of Sec. 4 depends on the scalar lattice). */
 ddflb_status ddflb_batch_set_run(ddflb_batch* b, double tol, int32_t steps_per_launch,
                                  double barrier_timeout_s, int32_t scalar_residual);
+/* Run settings of instance i, overriding the batch's: its own tolerance (tol
+ * >= 0; a negative tol returns to the batch's) and a step limit max_steps (> 0:
+ * at the first check at least max_steps steps after its last init, an
+ * instance that has not converged is frozen with DDFLB_INST_CAPPED; 0: no
+ * limit).  Kept across ddflb_batch_init; takes effect at the next check.
+ * E.g. one launch holds cold runs to 1e-8 next to long reference runs to
+ * 1e-10 capped at four times the cold steps.  Synchronises the stream. */
+ddflb_status ddflb_batch_set_instance_run(ddflb_batch* b, int32_t i, double tol,
+                                          int64_t max_steps);
+/* How a chunk of steps is launched.  0 (default): one persistent cooperative
+ * launch, every CTA walking its range of tiles step after step with a bounded
+ * device-wide barrier between steps (suits many small lattices, where a
+ * launch per step would cost more than the step).  1: one ordinary launch per
+ * step with one CTA per tile, then a check kernel (one CTA per instance, idle
+ * except at multiples of check_every) and at the end of the chunk a state-time
+ * update, all captured in one graph per chunk; no barrier, more resident warps
+ * (suits large batches).  Same results bit for bit.  The autotuner tries both. */
+ddflb_status ddflb_batch_set_schedule(ddflb_batch* b, int32_t schedule);
+ddflb_status ddflb_batch_get_schedule(const ddflb_batch* b, int32_t* schedule);
 /* Tile shape (32x4, 64x2, 128x1, 32x8, 64x4, 128x2, 256x1) and CTAs per SM
  * (0 = as many as fit); rebuilds the tile list.  Used by the autotuner. */
 ddflb_status ddflb_batch_set_tiles(ddflb_batch* b, int32_t tile_x, int32_t tile_y,
@@ -424,9 +444,10 @@ ddflb_status ddflb_batch_fields(ddflb_batch* b, int32_t i, float* rho, float* ux
  * run on it).  Synchronises; ETIMEOUT if a barrier wait ran out. */
 ddflb_status ddflb_batch_stats(ddflb_batch* b, double* residual, int32_t* flags,
                                int64_t* steps_to_tol, int64_t* state_time, int64_t* init_time);
-/* Autotuner: times every supported tile shape at full and half residency
- * (trial_steps per timed launch, CUDA events) and keeps the fastest; returns
- * the choice and its time per step.  Runs on zeroed populations, so it
+/* Autotuner: times every supported tile shape with the persistent launch at
+ * full and half residency and with one launch per step (trial_steps per timed
+ * chunk, CUDA events) and keeps the fastest (ddflb_batch_get_schedule tells
+ * which schedule); returns the tile shape, CTAs per SM and time per step.  Runs on zeroed populations, so it
  * OVERWRITES every instance's state and resets the time to 0: call it before
  * ddflb_batch_init.  Synchronises the stream. */
 ddflb_status ddflb_batch_autotune(ddflb_batch* b, int32_t trial_steps, int32_t* tile_x,

@@ -57,8 +57,10 @@ struct BatchStatus {
   int64_t steps_to_tol;  // state time at which the residual first fell below tol (-1: not yet)
   int64_t state_time;    // state time of the instance's current state when frozen
   long long init_time;   // state time at which the instance was (re)initialised
-  int32_t flags;         // DDFLB_INST_CONVERGED | DDFLB_INST_DIVERGED
+  int32_t flags;         // DDFLB_INST_CONVERGED | DDFLB_INST_DIVERGED | DDFLB_INST_CAPPED
   int32_t pad;
+  double tol;            // this instance's tolerance (< 0: the batch's)
+  int64_t max_steps;     // freeze after this many steps since init (0: no limit)
 };
 
 struct BatchSync {
@@ -141,7 +143,33 @@ __device__ bool grid_barrier(BatchSync* s, long long timeout_ns) {
   return ok != 0;
 }
 
-template <typename S, int BC>
+// Residual sums of one node at a check step (against the snapshot taken K
+// steps earlier), then its new snapshot (velocity and scalar).
+__device__ __forceinline__ void node_sums(const LbParams& P, const BatchInst& I, int x, int y,
+                                          const Mom& mf, const Macro& q, bool snap, bool check,
+                                          double acc[kParts]) {
+  const int64_t c = (int64_t)y * P.nx + x, n = (int64_t)P.nx * P.ny;
+  if (check) {
+    const double ex = (double)q.ux - I.uprev[c], ey = (double)q.uy - I.uprev[n + c];
+    const double ep = (double)q.phi - I.uprev[2 * n + c];
+    acc[0] += (double)q.ux * q.ux + (double)q.uy * q.uy;
+    acc[1] += ex * ex + ey * ey;
+    acc[2] += (double)mf.k0;
+    acc[3] += (double)q.phi * q.phi;
+    acc[4] += ep * ep;
+  }
+  if (snap) {
+    I.uprev[c] = q.ux;
+    I.uprev[n + c] = q.uy;
+    I.uprev[2 * n + c] = q.phi;
+  }
+}
+
+// COH: load through L2 only (the persistent kernel, whose planes other CTAs
+// rewrite within the launch); otherwise the read-only path (one step a launch)
+// SUMS: also the residual sums and the snapshot (at check steps); the
+// per-step schedule leaves them to k_batch_sums.
+template <typename S, int BC, bool COH, bool SUMS = true>
 __device__ __forceinline__ void batch_cell(const LbParams& P, const BatchInst& I, int src, int x,
                                            int y, bool inner, bool snap, bool check,
                                            double acc[kParts]) {
@@ -153,9 +181,9 @@ __device__ __forceinline__ void batch_cell(const LbParams& P, const BatchInst& I
   // a warp whose nodes all have their 8 neighbours inside the lattice pulls
   // without the wall rules (same addresses, so the same values)
   if (BC != BC_PERIODIC && inner)
-    pull<S, BC_PERIODIC, true>(P, fin, gin, x, y, df, dg);
+    pull<S, BC_PERIODIC, COH>(P, fin, gin, x, y, df, dg);
   else
-    pull<S, BC, true>(P, fin, gin, x, y, df, dg);
+    pull<S, BC, COH>(P, fin, gin, x, y, df, dg);
   const Mom mf = moments_flow(df), mg = moments_scalar(dg);
   const Macro q = macro(P, mf, mg);
   Neq nf = neq_flow(mf, q), ng = neq_scalar(P, mg, mf, q);
@@ -169,23 +197,7 @@ __device__ __forceinline__ void batch_cell(const LbParams& P, const BatchInst& I
     Codec<S>::store(fout + a * P.plane + o, df[a], P.sf);
     Codec<S>::store(gout + a * P.plane + o, dg[a], P.sg);
   }
-  if (check || snap) {
-    const int64_t c = (int64_t)y * P.nx + x, n = (int64_t)P.nx * P.ny;
-    if (check) {
-      const double ex = (double)q.ux - I.uprev[c], ey = (double)q.uy - I.uprev[n + c];
-      const double ep = (double)q.phi - I.uprev[2 * n + c];
-      acc[0] += (double)q.ux * q.ux + (double)q.uy * q.uy;
-      acc[1] += ex * ex + ey * ey;
-      acc[2] += (double)mf.k0;
-      acc[3] += (double)q.phi * q.phi;
-      acc[4] += ep * ep;
-    }
-    if (snap) {
-      I.uprev[c] = q.ux;
-      I.uprev[n + c] = q.uy;
-      I.uprev[2 * n + c] = q.phi;
-    }
-  }
+  if (SUMS && (check || snap)) node_sums(P, I, x, y, mf, q, snap, check, acc);
 }
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -199,6 +211,41 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   if (threadIdx.x == 0)
     for (int k = 0; k < nw; ++k) t += sh[k];
   return t;  // valid in thread 0
+}
+
+// Check of instance i after the step from state time t (a multiple of K): the
+// fixed-order reduction of its tiles' sums, then the freeze decision
+// (converged, diverged, or at its own step limit).  Called by one whole CTA.
+__device__ void check_instance(const BatchArgs& A, int i, int64_t t, double* sh) {
+  if (__ldcg(&A.ist[i].flags) != 0 || t - A.check_every < __ldcg(&A.ist[i].init_time)) return;
+  const int b = A.inst[i].tile_begin, e = A.inst[i].tile_end;
+  double v[kParts];
+  for (int k = 0; k < kParts; ++k) {
+    double a = 0.0;
+    for (int j = b + threadIdx.x; j < e; j += blockDim.x) a += __ldcg(&A.part[kParts * (int64_t)j + k]);
+    v[k] = block_sum(a, sh);
+  }
+  if (threadIdx.x == 0) {
+    BatchStatus& st = A.ist[i];
+    st.u2 = v[0];
+    st.mass_dev = v[2];
+    const double ru = v[0] > 0.0 ? sqrt(v[1] / v[0]) / A.check_every : 0.0;
+    const double rp = v[3] > 0.0 ? sqrt(v[4] / v[3]) / A.check_every : 0.0;
+    st.residual_phi = rp;
+    st.residual = A.scalar_residual ? fmax(ru, rp) : ru;
+    const double tol = st.tol >= 0.0 ? st.tol : A.tol;
+    if (!isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2]) || !isfinite(v[3])) {
+      st.flags = DDFLB_INST_DIVERGED;
+      st.state_time = t + 1;
+    } else if (tol > 0.0 && st.residual < tol) {
+      st.flags = DDFLB_INST_CONVERGED;
+      st.steps_to_tol = t - st.init_time;  // steps since this instance's init
+      st.state_time = t + 1;
+    } else if (st.max_steps > 0 && t + 1 - st.init_time >= st.max_steps) {
+      st.flags = DDFLB_INST_CAPPED;  // its own step limit, without convergence
+      st.state_time = t + 1;
+    }
+  }
 }
 
 // At most 64 registers a thread (4 CTAs of 256 threads or 8 of 128 per SM):
@@ -257,12 +304,12 @@ __global__ void __launch_bounds__(256, 4) k_batch(BatchArgs A) {
       if (x < sP.nx && y < sP.ny) {
         switch (sI.bc) {
           case BC_PERIODIC:
-            batch_cell<S, BC_PERIODIC>(sP, sI, src, x, y, inner, snap, check, acc);
+            batch_cell<S, BC_PERIODIC, true>(sP, sI, src, x, y, inner, snap, check, acc);
             break;
           case BC_CAVITY:
-            batch_cell<S, BC_CAVITY>(sP, sI, src, x, y, inner, snap, check, acc);
+            batch_cell<S, BC_CAVITY, true>(sP, sI, src, x, y, inner, snap, check, acc);
             break;
-          default: batch_cell<S, BC_CHANNEL>(sP, sI, src, x, y, inner, snap, check, acc);
+          default: batch_cell<S, BC_CHANNEL, true>(sP, sI, src, x, y, inner, snap, check, acc);
         }
       }
       if (check) {
@@ -274,40 +321,119 @@ __global__ void __launch_bounds__(256, 4) k_batch(BatchArgs A) {
     }
     if (check_t) {
       if (!grid_barrier(A.sync, A.timeout_ns)) return;
-      // per-instance fixed-order reduction of the tile sums
-      for (int i = blockIdx.x; i < A.ninst; i += gridDim.x) {
-        if (__ldcg(&A.ist[i].flags) != 0 || t - A.check_every < __ldcg(&A.ist[i].init_time)) continue;
-        const int b = A.inst[i].tile_begin, e = A.inst[i].tile_end;
-        double v[kParts];
-        for (int k = 0; k < kParts; ++k) {
-          double a = 0.0;
-          for (int j = b + threadIdx.x; j < e; j += blockDim.x) a += __ldcg(&A.part[kParts * (int64_t)j + k]);
-          v[k] = block_sum(a, sh);
-        }
-        if (threadIdx.x == 0) {
-          BatchStatus& st = A.ist[i];
-          st.u2 = v[0];
-          st.mass_dev = v[2];
-          const double ru = v[0] > 0.0 ? sqrt(v[1] / v[0]) / A.check_every : 0.0;
-          const double rp = v[3] > 0.0 ? sqrt(v[4] / v[3]) / A.check_every : 0.0;
-          st.residual_phi = rp;
-          st.residual = A.scalar_residual ? fmax(ru, rp) : ru;
-          if (!isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2]) || !isfinite(v[3])) {
-            st.flags = DDFLB_INST_DIVERGED;
-            st.state_time = t + 1;
-          } else if (A.tol > 0.0 && st.residual < A.tol) {
-            st.flags = DDFLB_INST_CONVERGED;
-            st.steps_to_tol = t - st.init_time;  // steps since this instance's init
-            st.state_time = t + 1;
-          }
-        }
-      }
+      for (int i = blockIdx.x; i < A.ninst; i += gridDim.x) check_instance(A, i, t, sh);
       cur = -1;  // re-read the activity flags
     }
     if (s == 0 && (int)blockIdx.x == A.skip_block) return;  // test hook: never arrive
     if (!grid_barrier(A.sync, A.timeout_ns)) return;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) A.sync->step = t0 + A.nsteps;
+}
+
+// Schedule 1: one ordinary launch per time step, one CTA per tile, then (idle
+// except at check steps) the sums and check kernels and, at the end of a
+// chunk, the state-time update, all captured in one graph per chunk.  No
+// device-wide barrier: the stream orders the steps.  Step s of the chunk
+// advances the state from time sync->step + s.  The node update carries no
+// check code; at most 56 registers, so 9 CTAs of 128 threads stay resident.
+template <typename S>
+__global__ void __maxnreg__(56) k_batch_tile(BatchArgs A, int s) {
+  __shared__ BatchInst sI;
+  __shared__ int sActive;
+  const int64_t t = A.sync->step + s;
+  const int4 T = __ldg(&A.tiles[blockIdx.x]);
+  const int* srcw = (const int*)(A.inst + T.x);
+  int* dstw = (int*)&sI;
+  for (int w = threadIdx.x; w < (int)(sizeof(BatchInst) / 4); w += blockDim.x) dstw[w] = __ldg(&srcw[w]);
+  if (threadIdx.x == 0) sActive = __ldcg(&A.ist[T.x].flags) == 0;
+  __syncthreads();
+  if (!sActive) return;  // uniform over the CTA
+  const LbParams& sP = sI.P;
+  const int src = (int)(t & 1);
+  const int tx = threadIdx.x % A.tile_x, ty = threadIdx.x / A.tile_x;
+  const int x = T.y + tx, y = T.z + ty;
+  const bool in_x = sI.bc == BC_CHANNEL ? x < sP.nx : (x >= 1 && x < sP.nx - 1);
+  const bool inner = __all_sync(0xffffffffu, in_x && y >= 1 && y < sP.ny - 1);
+  if (x >= sP.nx || y >= sP.ny) return;
+  double none[kParts];
+  switch (sI.bc) {
+    case BC_PERIODIC:
+      batch_cell<S, BC_PERIODIC, false, false>(sP, sI, src, x, y, inner, false, false, none);
+      break;
+    case BC_CAVITY:
+      batch_cell<S, BC_CAVITY, false, false>(sP, sI, src, x, y, inner, false, false, none);
+      break;
+    default: batch_cell<S, BC_CHANNEL, false, false>(sP, sI, src, x, y, inner, false, false, none);
+  }
+}
+
+// At a check step (state time t a multiple of K, after the step from t): the
+// residual sums of each tile from the state at time t, read back from the
+// step's source buffer (the step wrote the other one), and the new snapshot.
+// A grid of a few CTAs per SM walks the tiles; at other steps it returns.
+template <typename S>
+__global__ void __launch_bounds__(256) k_batch_sums(BatchArgs A, int s) {
+  __shared__ BatchInst sI;
+  __shared__ double sh[8];
+  __shared__ int sActive;
+  __shared__ long long sInit;
+  const int64_t t = A.sync->step + s;
+  const bool snap = A.check_every > 0 && t % A.check_every == 0;
+  if (!snap) return;
+  const LbParams& sP = sI.P;
+  const int src = (int)(t & 1);
+  const int tx = threadIdx.x % A.tile_x, ty = threadIdx.x / A.tile_x;
+  int cur = -1;
+  for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
+    const int4 T = __ldg(&A.tiles[tile]);
+    if (T.x != cur) {
+      __syncthreads();
+      const int* srcw = (const int*)(A.inst + T.x);
+      int* dstw = (int*)&sI;
+      for (int w = threadIdx.x; w < (int)(sizeof(BatchInst) / 4); w += blockDim.x) dstw[w] = __ldg(&srcw[w]);
+      if (threadIdx.x == 0) {
+        // the flag as it was before this step's check (the check kernel runs next)
+        sActive = __ldcg(&A.ist[T.x].flags) == 0;
+        sInit = __ldcg(&A.ist[T.x].init_time);
+      }
+      cur = T.x;
+      __syncthreads();
+    }
+    if (!sActive) continue;
+    const bool check = t > 0 && t - A.check_every >= sInit;
+    const int x = T.y + tx, y = T.z + ty;
+    double acc[kParts] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (x < sP.nx && y < sP.ny) {
+      const S* fin = (const S*)sI.buf[src];
+      float df[9], dg[9];
+      switch (sI.bc) {
+        case BC_PERIODIC: pull<S, BC_PERIODIC>(sP, fin, fin + sI.goff, x, y, df, dg); break;
+        case BC_CAVITY: pull<S, BC_CAVITY>(sP, fin, fin + sI.goff, x, y, df, dg); break;
+        default: pull<S, BC_CHANNEL>(sP, fin, fin + sI.goff, x, y, df, dg);
+      }
+      const Mom mf = moments_flow(df), mg = moments_scalar(dg);
+      node_sums(sP, sI, x, y, mf, macro(sP, mf, mg), true, check, acc);
+    }
+    if (check) {
+      for (int k = 0; k < kParts; ++k) {
+        const double v = block_sum(acc[k], sh);
+        if (threadIdx.x == 0) A.part[kParts * (int64_t)tile + k] = v;
+      }
+    }
+  }
+}
+
+// The checks after step s of a chunk (a no-op unless its state time is a
+// positive multiple of K): one CTA per instance.
+__global__ void __launch_bounds__(256) k_batch_check(BatchArgs A, int s) {
+  __shared__ double sh[8];
+  const int64_t t = A.sync->step + s;
+  if (!(A.check_every > 0 && t > 0 && t % A.check_every == 0)) return;
+  check_instance(A, blockIdx.x, t, sh);
+}
+
+__global__ void k_batch_advance(BatchSync* sync, int nsteps) {
+  if (threadIdx.x == 0) sync->step += nsteps;
 }
 
 }  // namespace ddflb
@@ -400,6 +526,10 @@ struct ddflb_batch {
   cudaGraphExec_t graph;
   int graph_chunk;
   bool graph_failed;
+  std::vector<double> inst_tol;   // per-instance tolerance (< 0: the batch's)
+  std::vector<int64_t> inst_cap;  // per-instance step limit (0: none)
+  int schedule;                   // 0 persistent cooperative launch, 1 one launch per step
+  int sums_grid;                  // CTAs of the check-step sums kernel (schedule 1)
 };
 
 namespace {
@@ -432,11 +562,14 @@ ddflb_status upload_tiles(ddflb_batch* b) {
 }
 
 template <typename S>
-void* kernel_ptr() { return (void*)k_batch<S>; }
+void* kernel_ptr(int schedule) {
+  return schedule == 1 ? (void*)k_batch_tile<S> : (void*)k_batch<S>;
+}
 
-void* batch_kernel(int storage) {
-  return storage == 0 ? kernel_ptr<float>() : storage == 1 ? kernel_ptr<__half>()
-                                                            : kernel_ptr<__nv_bfloat16>();
+void* batch_kernel(int storage, int schedule = 0) {
+  return storage == 0 ? kernel_ptr<float>(schedule)
+                      : storage == 1 ? kernel_ptr<__half>(schedule)
+                                     : kernel_ptr<__nv_bfloat16>(schedule);
 }
 
 ddflb_status configure(ddflb_batch* b, int tx, int ty, int bps) {
@@ -445,13 +578,15 @@ ddflb_status configure(ddflb_batch* b, int tx, int ty, int bps) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   int occ = 0;
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel(b->storage), tx * ty, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel(b->storage, b->schedule),
+                                                      tx * ty, 0);
   if (e != cudaSuccess) return bcuda(e, "batch occupancy");
   if (occ < 1) return bfail(DDFLB_EINVAL, "batch kernel cannot be resident with %d threads", tx * ty);
   b->tile_x = tx;
   b->tile_y = ty;
   b->blocks_per_sm = bps > 0 ? std::min(bps, occ) : occ;
   b->grid = b->blocks_per_sm * nsm;
+  b->sums_grid = 4 * nsm;
   if (b->graph) {
     cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
@@ -481,6 +616,23 @@ BatchArgs args_for(ddflb_batch* b, int nsteps) {
 
 cudaError_t launch_chunk(ddflb_batch* b, cudaStream_t s, int nsteps) {
   BatchArgs A = args_for(b, nsteps);
+  if (b->schedule == 1) {
+    // one launch per step (+ the check kernel), then the state-time update
+    const dim3 tb(b->tile_x * b->tile_y);
+    void* sums = b->storage == 0 ? (void*)k_batch_sums<float>
+               : b->storage == 1 ? (void*)k_batch_sums<__half> : (void*)k_batch_sums<__nv_bfloat16>;
+    for (int k = 0; k < nsteps; ++k) {
+      void* targs[] = {&A, &k};
+      cudaError_t e = cudaLaunchKernel(batch_kernel(b->storage, 1), dim3(b->ntiles), tb, targs, 0, s);
+      if (e == cudaSuccess) e = cudaLaunchKernel(sums, dim3(b->sums_grid), tb, targs, 0, s);
+      if (e != cudaSuccess) return e;
+      k_batch_check<<<b->n, 256, 0, s>>>(A, k);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    k_batch_advance<<<1, 32, 0, s>>>(b->d_sync, nsteps);
+    return cudaGetLastError();
+  }
   void* kargs[] = {&A};
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(b->grid);
@@ -586,16 +738,20 @@ ddflb_status ddflb_batch_create(int32_t n, const ddflb_params* p, void* ws, size
   b->d_sync = (BatchSync*)(b->ws + b->lay.off_sync);
   b->graph = nullptr;
   b->graph_failed = false;
+  b->schedule = 0;
   cudaError_t e = cudaMemsetAsync(b->d_sync, 0, sizeof(BatchSync), b->stream);
   if (e != cudaSuccess) {
     delete b;
     return bcuda(e, "batch create");
   }
+  b->inst_tol.assign(n, -1.0);
+  b->inst_cap.assign(n, 0);
   std::vector<BatchStatus> st(n);
   for (auto& s : st) {
     std::memset(&s, 0, sizeof s);
     s.steps_to_tol = -1;
     s.residual = NAN;
+    s.tol = -1.0;
   }
   e = cudaMemcpyAsync(b->d_status, st.data(), n * sizeof(BatchStatus), cudaMemcpyHostToDevice,
                       b->stream);
@@ -626,6 +782,37 @@ ddflb_status ddflb_batch_set_run(ddflb_batch* b, double tol, int32_t steps_per_l
     cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
   }
+  return DDFLB_OK;
+}
+
+ddflb_status ddflb_batch_set_instance_run(ddflb_batch* b, int32_t i, double tol,
+                                          int64_t max_steps) {
+  if (!b || i < 0 || i >= b->n) return bfail(DDFLB_EINVAL, "bad batch or instance index");
+  if (!(tol == tol) || max_steps < 0) return bfail(DDFLB_EINVAL, "tol is NaN or max_steps < 0");
+  b->inst_tol[i] = tol;
+  b->inst_cap[i] = max_steps;
+  // also into the live status (takes effect at the next check; the rest of
+  // the status is left as it is)
+  BatchStatus* d = b->d_status + i;
+  cudaError_t e = cudaMemcpyAsync(&d->tol, &b->inst_tol[i], sizeof(double),
+                                  cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&d->max_steps, &b->inst_cap[i], sizeof(int64_t), cudaMemcpyHostToDevice,
+                        b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  return e == cudaSuccess ? DDFLB_OK : bcuda(e, "batch instance run");
+}
+
+ddflb_status ddflb_batch_set_schedule(ddflb_batch* b, int32_t schedule) {
+  if (!b) return bfail(DDFLB_EINVAL, "NULL batch");
+  if (schedule != 0 && schedule != 1) return bfail(DDFLB_EINVAL, "schedule must be 0 or 1");
+  b->schedule = schedule;
+  return configure(b, b->tile_x, b->tile_y, schedule == 1 ? 0 : b->blocks_per_sm);
+}
+
+ddflb_status ddflb_batch_get_schedule(const ddflb_batch* b, int32_t* schedule) {
+  if (!b || !schedule) return bfail(DDFLB_EINVAL, "NULL argument");
+  *schedule = b->schedule;
   return DDFLB_OK;
 }
 
@@ -675,6 +862,8 @@ ddflb_status ddflb_batch_init(ddflb_batch* b, int32_t i, const float* rho, const
   s.steps_to_tol = -1;
   s.residual = NAN;
   s.init_time = b->step;
+  s.tol = b->inst_tol[i];
+  s.max_steps = b->inst_cap[i];
   e = cudaMemcpyAsync(b->d_status + i, &s, sizeof s, cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   return e == cudaSuccess ? DDFLB_OK : bcuda(e, "batch init status");
@@ -770,20 +959,27 @@ ddflb_status ddflb_batch_autotune(ddflb_batch* b, int32_t trial_steps, int32_t* 
     std::memset(&x, 0, sizeof x);
     x.steps_to_tol = -1;
     x.residual = NAN;
+    x.tol = -1.0;  // during the trials: the batch tolerance, 0 (nothing freezes)
   }
+  e = cudaMemcpyAsync(b->d_status, st.data(), b->n * sizeof(BatchStatus), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return bcuda(e, "autotune status");
   const double tol = b->tol;
   b->tol = 0.0;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   float best = 1e30f;
-  int bx = 128, by = 1, bb = 0;
+  int bx = 128, by = 1, bb = 0, bs = 0;
   ddflb_status rs = DDFLB_OK;
+  const int saved_schedule = b->schedule;
+  // candidates per tile shape: the persistent launch at full and half
+  // residency (variant 0, 1), and one launch per step (variant 2)
   for (int k = 0; k < kNumShapes && rs == DDFLB_OK; ++k) {
-    for (int half = 0; half < 2 && rs == DDFLB_OK; ++half) {
+    for (int half = 0; half < 3 && rs == DDFLB_OK; ++half) {
+      b->schedule = half == 2 ? 1 : 0;
       rs = configure(b, kShapes[k][0], kShapes[k][1], 0);
       if (rs != DDFLB_OK) break;
-      if (half) {
+      if (half == 1) {
         if (b->blocks_per_sm < 2) continue;
         rs = configure(b, kShapes[k][0], kShapes[k][1], b->blocks_per_sm / 2);
         if (rs != DDFLB_OK) break;
@@ -804,16 +1000,25 @@ ddflb_status ddflb_batch_autotune(ddflb_batch* b, int32_t trial_steps, int32_t* 
         bx = b->tile_x;
         by = b->tile_y;
         bb = b->blocks_per_sm;
+        bs = b->schedule;
       }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   b->tol = tol;
-  if (rs != DDFLB_OK) return rs;
+  if (rs != DDFLB_OK) {
+    b->schedule = saved_schedule;
+    return rs;
+  }
+  b->schedule = bs;
   rs = configure(b, bx, by, bb);
   if (rs != DDFLB_OK) return rs;
-  // back to a clean state at time 0
+  // back to a clean state at time 0, with the per-instance run settings
+  for (int i = 0; i < b->n; ++i) {
+    st[i].tol = b->inst_tol[i];
+    st[i].max_steps = b->inst_cap[i];
+  }
   e = cudaMemsetAsync(b->ws, 0, b->lay.off_inst, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_sync, 0, sizeof(BatchSync), s);
   if (e == cudaSuccess)

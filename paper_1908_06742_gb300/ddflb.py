@@ -88,6 +88,10 @@ SIGNATURES = {
     "ddflb_batch_set_run": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_int32, ctypes.c_double,
                                            ctypes.c_int32]),
     "ddflb_batch_set_tiles": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "ddflb_batch_set_instance_run": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_double,
+                                                    ctypes.c_int64]),
+    "ddflb_batch_set_schedule": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "ddflb_batch_get_schedule": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32)]),
     "ddflb_batch_get_tiles": (ctypes.c_int, [_VP] + [ctypes.POINTER(ctypes.c_int32)] * 3),
     "ddflb_batch_init": (ctypes.c_int, [_VP, ctypes.c_int32, _FP, _FP, _FP, _FP, _FP]),
     "ddflb_batch_step": (ctypes.c_int, [_VP, ctypes.c_int64]),
@@ -143,7 +147,7 @@ SIGNATURES = {
     "ddflb_version": (ctypes.c_char_p, []),
 }
 
-INST_CONVERGED, INST_DIVERGED = 1, 2
+INST_CONVERGED, INST_DIVERGED, INST_CAPPED = 1, 2, 4
 
 
 def load(path: str = LIB_PATH):
@@ -569,6 +573,25 @@ class Batch:
         _check(self.lib.ddflb_batch_set_tiles(self._h, tile_x, tile_y, blocks_per_sm))
         return self
 
+    def set_schedule(self, schedule: int):
+        """0: one persistent cooperative launch per chunk of steps (device-wide
+        barrier between steps); 1: one launch per step and tile-per-CTA, the
+        chunk captured as a graph.  Same results."""
+        _check(self.lib.ddflb_batch_set_schedule(self._h, int(schedule)))
+        return self
+
+    def schedule(self) -> int:
+        v = ctypes.c_int32()
+        _check(self.lib.ddflb_batch_get_schedule(self._h, ctypes.byref(v)))
+        return v.value
+
+    def set_instance_run(self, i, tol=-1.0, max_steps=0):
+        """Instance i's own tolerance (negative: the batch's) and step limit
+        (0: none); a limited instance that has not converged is frozen with
+        INST_CAPPED."""
+        _check(self.lib.ddflb_batch_set_instance_run(self._h, int(i), float(tol), int(max_steps)))
+        return self
+
     def tiles(self):
         v = [ctypes.c_int32() for _ in range(3)]
         _check(self.lib.ddflb_batch_get_tiles(self._h, *[ctypes.byref(x) for x in v]))
@@ -616,13 +639,14 @@ class Batch:
         from . import tuning
         key = tuning.key("batch", self.cfgs)
         hit = tuning.lookup(key) if cache else None
-        if hit:
-            return self.set_tiles(*hit["choice"]), hit
+        if hit and len(hit["choice"]) == 4:
+            self.set_schedule(hit["choice"][3])
+            return self.set_tiles(*hit["choice"][:3]), hit
         v = [ctypes.c_int32() for _ in range(3)]
         ms = ctypes.c_double()
         _check(self.lib.ddflb_batch_autotune(self._h, int(trial_steps),
                                              *[ctypes.byref(x) for x in v], ctypes.byref(ms)))
-        rec = {"choice": [x.value for x in v], "ms_per_step": ms.value}
+        rec = {"choice": [x.value for x in v] + [self.schedule()], "ms_per_step": ms.value}
         if cache:
             tuning.store(key, rec)
         return self, rec

@@ -379,23 +379,47 @@ def steady_fields(b, i):
     return {k: v.double().cpu().numpy() for k, v in f.items()}
 
 
-def train(net, X, T, epochs, lr=1e-3, seed=0, log=None):
+def _grad_tensors(net):
+    return [t for name, _, _ in net.specs for t in (net.p[name]["gw"], net.p[name]["gb"])]
+
+
+def _min_over_ranks(v: int, world: int, device) -> int:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MIN)
+    return int(t.item())
+
+
+def train(net, X, T, epochs, lr=1e-3, seed=0, log=None, world=1, rank=0):
     """Adam on minibatches of (inputs X [N,n,n,16] BF16, targets T [N,n,n,8]
-    FP32), both on the device.  Returns the loss history (per epoch)."""
+    FP32), both on the device.  Data parallel over `world` ranks: each rank
+    holds its own part of the training set, computes the gradient of its
+    minibatch and the ranks average the gradients before every Adam step, so
+    their weights stay identical (one step = a global batch of world x B).
+    Returns the loss history (per epoch, this rank's last minibatch)."""
+    from .distributed import average_gradients
     torch = net.torch
-    g = torch.Generator().manual_seed(seed)
+    g = torch.Generator().manual_seed(seed * 1000 + rank)
     hist = []
     N = X.shape[0]
-    steps_per_epoch = max(1, N // net.B)
+    # every rank takes the same number of steps (the collectives stay in step)
+    steps_per_epoch = max(1, _min_over_ranks(N // net.B, world, X.device))
     total = epochs * steps_per_epoch
+    grads = _grad_tensors(net)
     k = 0
     for ep in range(epochs):
         perm = torch.randperm(N, generator=g)
         acc = 0.0
         for s in range(steps_per_epoch):
             idx = perm[s * net.B:(s + 1) * net.B].to(X.device)
+            if idx.numel() < net.B:  # a rank with fewer samples than a batch repeats them
+                idx = idx.repeat((net.B + idx.numel() - 1) // idx.numel())[:net.B]
             net.forward(X.index_select(0, idx))
             loss = net.backward(T.index_select(0, idx).contiguous())
+            average_gradients(grads, world)
             # cosine decay of the learning rate
             net.adam(lr=lr * 0.5 * (1 + math.cos(math.pi * k / total)))
             acc += float(loss.item()) if s == steps_per_epoch - 1 else 0.0
@@ -418,86 +442,190 @@ def predict(net, X):
     return torch.cat(outs)[:X.shape[0]]
 
 
+def _rest(n):
+    return (np.ones((n, n), np.float32), np.zeros((n, n), np.float32),
+            np.zeros((n, n), np.float32), np.zeros((n, n), np.float32), None)
+
+
+def warm_fields(pred_k, d):
+    """Device init fields of one cavity from its prediction [n, n, 8]
+    (ddflb_warm_fields: rescale, central differences, S_xy / omega split)."""
+    return D.warm_fields(pred_k.contiguous(), d["u"], OMEGA_SCALE, 0.0, 1.0)
+
+
+def _inputs(ds, n, device):
+    import torch
+    return torch.from_numpy(np.stack([input_planes(d, n) for d in ds])).to(torch.bfloat16).to(device)
+
+
+def _steady_data(ds, n, starts, tol, max_steps, device):
+    """Run the cavities `ds` from `starts` to the tolerance in one batch; the
+    converged ones become training pairs (input planes, targets)."""
+    b, st = run_to_steady([cavity_config(d, n) for d in ds], starts, tol=tol,
+                          max_steps=max_steps, device=device)
+    ok = [i for i in range(len(ds)) if st["flags"][i] == D.INST_CONVERGED]
+    X = np.stack([input_planes(ds[i], n) for i in ok]) if ok else np.zeros((0, n, n, CIN), np.float32)
+    T = np.stack([targets(steady_fields(b, i), ds[i], n) for i in ok]) if ok else np.zeros((0, n, n, COUT), np.float32)
+    steps = [int(st["steps_to_tol"][i]) for i in ok]
+    del b
+    return X, T, steps
+
+
+def _omega_err(f, ref):
+    a, r = f["omega"], ref["omega"]
+    m = np.isfinite(a) & np.isfinite(r)
+    return float(np.linalg.norm((a - r)[m]) / np.linalg.norm(r[m]))
+
+
 def experiment(n=128, n_train=512, n_test=64, epochs=60, batch=16, c=32, seed=1, tol=1e-8,
-               max_steps=2_000_000, device="cuda", log=print):
-    """The learned warm start, end to end: steady training data from the
-    method, GPU training, then held-out cavities run to the tolerance from a
-    cold start (rest) and from the network's prediction."""
+               max_steps=2_000_000, device="cuda", log=print, boot=0, boot_epochs=None,
+               ref_tol=1e-10, ref_factor=4, world=None, rank=None):
+    """The learned warm start, end to end, data parallel over the ranks of an
+    initialised process group (every rank holds its share of the draws):
+
+    1. training data: the method's own steady solutions.  With boot > 0 the
+       first `boot` draws run cold (from rest), a network trained on them
+       warm-starts the remaining draws, and every draw still runs to the
+       tolerance, so the data are the method's results either way;
+    2. training on the GPU with the library's kernels (gradients averaged
+       over ranks);
+    3. held-out draws run to the tolerance from rest (cold) and from the
+       network's prediction (warm), next to a long-run reference from rest
+       (tolerance ref_tol, at most ref_factor times the cold run's steps), in
+       one batch.  A run that hits the step cap counts at the cap.
+
+    Returns the summary on rank 0 (per-case rows in global order) and None on
+    the other ranks."""
     import time
     import torch
+    from .distributed import gather_indexed, shard_indices, world_and_rank
+    if world is None or rank is None:
+        world, rank = world_and_rank()
     t0 = time.perf_counter()
     tr, te = draws(n_train, seed), draws(n_test, seed + 1000)
-    rest = lambda: (np.ones((n, n), np.float32), np.zeros((n, n), np.float32),
-                    np.zeros((n, n), np.float32), np.zeros((n, n), np.float32), None)
-    # 1. training data: the method's own steady solutions (cold starts)
-    b, st = run_to_steady([cavity_config(d, n) for d in tr], [rest() for _ in tr], tol=tol,
-                          max_steps=max_steps, device=device)
-    ok = [i for i in range(len(tr)) if st["flags"][i] == D.INST_CONVERGED]
-    X = np.stack([input_planes(tr[i], n) for i in ok])
-    T = np.stack([targets(steady_fields(b, i), tr[i], n) for i in ok])
-    del b
-    t_data = time.perf_counter() - t0
-    log(f"data: {len(ok)}/{len(tr)} converged in {t_data:.1f} s")
-    # 2. training on the GPU with the library's kernels
+    mine_tr = shard_indices(len(tr), rank, world)
+    mine_te = shard_indices(len(te), rank, world)
+    n_boot = 0 if boot <= 0 else len(shard_indices(min(boot, n_train), rank, world))
     net = UNet(c=c, batch=batch, H=n, W=n, device=device, seed=seed)
-    Xd = torch.from_numpy(X).to(torch.bfloat16).to(device)
-    Td = torch.from_numpy(T).to(device)
-    t1 = time.perf_counter()
-    hist = train(net, Xd, Td, epochs, log=lambda e, l: log(f"epoch {e} loss {l:.4e}") if e % 10 == 0 else None)
+    # 1. training data (this rank's share)
+    d_cold = [tr[i] for i in mine_tr[:n_boot]] if n_boot else [tr[i] for i in mine_tr]
+    Xc, Tc, steps_c = _steady_data(d_cold, n, [_rest(n) for _ in d_cold], tol, max_steps, device)
+    t_cold = time.perf_counter() - t0
+    log(f"rank {rank}: {len(steps_c)}/{len(d_cold)} cold cavities converged in {t_cold:.1f} s")
+    X_all, T_all, steps_w, t_boot_train, t_warm = Xc, Tc, [], 0.0, 0.0
+    if n_boot:
+        Xd = torch.from_numpy(Xc).to(torch.bfloat16).to(device)
+        Td = torch.from_numpy(Tc).to(device)
+        t1 = time.perf_counter()
+        train(net, Xd, Td, boot_epochs or epochs, world=world, rank=rank)
+        torch.cuda.synchronize()
+        t_boot_train = time.perf_counter() - t1
+        del Xd, Td
+        d_warm = [tr[i] for i in mine_tr[n_boot:]]
+        t2 = time.perf_counter()
+        pred = predict(net, _inputs(d_warm, n, device)) if d_warm else None
+        starts = [warm_fields(pred[k], d) for k, d in enumerate(d_warm)]
+        del pred
+        Xw, Tw, steps_w = _steady_data(d_warm, n, starts, tol, max_steps, device)
+        del starts
+        t_warm = time.perf_counter() - t2
+        log(f"rank {rank}: {len(steps_w)}/{len(d_warm)} warm-started cavities converged in {t_warm:.1f} s")
+        X_all, T_all = np.concatenate([Xc, Xw]), np.concatenate([Tc, Tw])
+    # 2. training on everything this rank holds
+    Xd = torch.from_numpy(X_all).to(torch.bfloat16).to(device)
+    Td = torch.from_numpy(T_all).to(device)
+    del X_all, T_all
+    t3 = time.perf_counter()
+    hist = train(net, Xd, Td, epochs, seed=seed + 1, world=world, rank=rank,
+                 log=lambda e, l: log(f"epoch {e} loss {l:.4e}") if e % 10 == 0 and rank == 0 else None)
     torch.cuda.synchronize()
-    t_train = time.perf_counter() - t1
-    # 3. held-out: cold start and warm start side by side in one batch
-    Xt = torch.from_numpy(np.stack([input_planes(d, n) for d in te])).to(torch.bfloat16).to(device)
-    pred = predict(net, Xt).cpu().numpy()
-    cfgs = [cavity_config(d, n) for d in te] * 2
-    starts = [rest() for _ in te] + [warm_start(pred[k], te[k], n) for k in range(len(te))]
-    b, st = run_to_steady(cfgs, starts, tol=tol, max_steps=max_steps, device=device)
-    rows = []
-    for k in range(len(te)):
-        fc, fw = st["flags"][k], st["flags"][k + len(te)]
-        if fc != D.INST_CONVERGED or fw != D.INST_CONVERGED:
-            rows.append(dict(k=k, cold=int(st["steps_to_tol"][k]), warm=int(st["steps_to_tol"][k + len(te)]),
-                             ok=False))
-            continue
-        cold, warm = steady_fields(b, k), steady_fields(b, k + len(te))
-        om_c, om_w = np.nan_to_num(cold["omega"]), np.nan_to_num(warm["omega"])
-        mask = np.isfinite(cold["omega"]) & np.isfinite(warm["omega"])
-        e_om = float(np.linalg.norm((om_w - om_c)[mask]) / np.linalg.norm(om_c[mask]))
-        tgt = targets(cold, te[k], n)
-        e_pred = float(np.linalg.norm(pred[k][..., :4] - tgt[..., :4]) / np.linalg.norm(tgt[..., :4]))
-        rows.append(dict(k=k, cold=int(st["steps_to_tol"][k]), warm=int(st["steps_to_tol"][k + len(te)]),
-                         ok=True, omega_rel_diff=e_om, pred_rel_err=e_pred, **te[k]))
-    good = [r for r in rows if r["ok"]]
-    cold_sum = sum(r["cold"] for r in good)
-    warm_sum = sum(r["warm"] for r in good)
-    ratios = [r["cold"] / max(r["warm"], 1) for r in good]
+    t_train = time.perf_counter() - t3
+    n_train_ok = int(round(_sum_over_ranks(float(Xd.shape[0]), world, device)))
+    del Xd, Td
+    # 3. held-out: cold, warm and the long-run reference side by side
+    ds = [te[i] for i in mine_te]
+    rows = {}
+    if ds:
+        t4 = time.perf_counter()
+        pred = predict(net, _inputs(ds, n, device))
+        k_ = len(ds)
+        cfgs = [cavity_config(d, n) for d in ds] * 2
+        starts = [_rest(n) for _ in ds] + [warm_fields(pred[k], d) for k, d in enumerate(ds)]
+        b, st = run_to_steady(cfgs, starts, tol=tol, max_steps=max_steps, device=device)
+        capped = lambda i: int(st["steps_to_tol"][i]) if st["flags"][i] == D.INST_CONVERGED else max_steps
+        cold = [capped(k) for k in range(k_)]
+        warm = [capped(k + k_) for k in range(k_)]
+        fc = [steady_fields(b, k) for k in range(k_)]
+        fw = [steady_fields(b, k + k_) for k in range(k_)]
+        ok_c = [bool(st["flags"][k] == D.INST_CONVERGED) for k in range(k_)]
+        ok_w = [bool(st["flags"][k + k_] == D.INST_CONVERGED) for k in range(k_)]
+        del b
+        # long-run reference from rest: ref_tol, at most ref_factor x the cold steps
+        rb = D.Batch([cavity_config(d, n) for d in ds], device=device).set_run(
+            tol=ref_tol, steps_per_launch=2000, scalar_residual=True)
+        rb.autotune(trial_steps=4, cache=True)
+        for k in range(k_):
+            rb.set_instance_run(k, ref_tol, ref_factor * cold[k])
+            rb.init(k, *_rest(n))
+        while True:
+            rb.step(20000)
+            rs = rb.stats()
+            if (rs["flags"] != 0).all():
+                break
+        fr = [steady_fields(rb, k) for k in range(k_)]
+        rsteps = [int(rs["state_time"][k] - rs["init_time"][k]) for k in range(k_)]
+        del rb
+        t_eval = time.perf_counter() - t4
+        for k, d in enumerate(ds):
+            tgt = targets(fc[k], d, n)
+            pk = pred[k].float().cpu().numpy()
+            rows[mine_te[k]] = dict(
+                k=mine_te[k], cold=cold[k], warm=warm[k], cold_converged=ok_c[k],
+                warm_converged=ok_w[k], ratio=cold[k] / max(warm[k], 1),
+                omega_err_cold=_omega_err(fc[k], fr[k]), omega_err_warm=_omega_err(fw[k], fr[k]),
+                omega_rel_diff=_omega_err(fw[k], fc[k]), ref_steps=rsteps[k],
+                ref_converged=bool(rs["flags"][k] == D.INST_CONVERGED),
+                pred_rel_err=float(np.linalg.norm(pk[..., :4] - tgt[..., :4]) /
+                                   np.linalg.norm(tgt[..., :4])), **d)
+        log(f"rank {rank}: held-out evaluation in {t_eval:.1f} s")
+    timing = dict(data_cold=t_cold, boot_train=t_boot_train, data_warm=t_warm, train=t_train)
+    allrows = gather_indexed(rows, world)
+    times = gather_indexed({rank: timing}, world)
+    data_steps = gather_indexed({rank: (sum(steps_c), len(steps_c), sum(steps_w), len(steps_w))}, world)
+    if allrows is None:
+        return None
+    ratios = [r["ratio"] for r in allrows]
+    cold_sum = sum(r["cold"] for r in allrows)
+    warm_sum = sum(r["warm"] for r in allrows)
+    med = lambda v: float(np.median(v)) if v else None
+    sc = sum(x[0] for x in data_steps); nc = sum(x[1] for x in data_steps)
+    sw = sum(x[2] for x in data_steps); nw = sum(x[3] for x in data_steps)
     return dict(
-        grid=n, n_train=len(ok), n_train_drawn=len(tr), n_test=len(te), n_test_both_converged=len(good),
+        grid=n, world=world, n_train=n_train_ok, n_train_drawn=len(tr), n_boot=min(boot, n_train),
+        n_test=len(te), n_test_cold_converged=sum(r["cold_converged"] for r in allrows),
+        n_test_warm_converged=sum(r["warm_converged"] for r in allrows),
+        n_test_both_converged=sum(r["cold_converged"] and r["warm_converged"] for r in allrows),
         params=net.numel, epochs=epochs, final_loss=hist[-1] if hist else None,
         steps_cold_total=cold_sum, steps_warm_total=warm_sum,
-        steps_saved_ratio=cold_sum / max(warm_sum, 1),
-        median_ratio=float(np.median(ratios)) if ratios else None,
-        omega_rel_diff_max=max((r["omega_rel_diff"] for r in good), default=None),
-        pred_rel_err_median=float(np.median([r["pred_rel_err"] for r in good])) if good else None,
-        seconds_data=t_data, seconds_train=t_train, rows=rows)
+        steps_saved_ratio=cold_sum / max(warm_sum, 1), median_ratio=med(ratios),
+        capped_counted_at=max_steps,
+        omega_err_cold_median=med([r["omega_err_cold"] for r in allrows]),
+        omega_err_warm_median=med([r["omega_err_warm"] for r in allrows]),
+        omega_err_cold_max=max(r["omega_err_cold"] for r in allrows),
+        omega_err_warm_max=max(r["omega_err_warm"] for r in allrows),
+        omega_rel_diff_max=max(r["omega_rel_diff"] for r in allrows),
+        ref_tol=ref_tol, ref_factor=ref_factor,
+        ref_converged=sum(r["ref_converged"] for r in allrows),
+        pred_rel_err_median=med([r["pred_rel_err"] for r in allrows]),
+        data_steps_cold_mean=sc / max(nc, 1), data_steps_warm_mean=sw / max(nw, 1),
+        seconds=max(sum(t.values()) for t in times), timing_rank0=times[0], rows=allrows)
 
 
-def warm_start(pred, d, n):
-    """Initial fields from a prediction [n, n, 8]: velocity, scalar, density and
-    the gradients for the non-equilibrium part.  Diagonal derivatives and S_xy
-    come from central differences of the predicted velocity (initial state
-    only); the antisymmetric part from the predicted vorticity."""
-    U = d["u"]
-    ux = pred[..., 0] * U
-    uy = pred[..., 1] * U
-    phi = np.clip(pred[..., 2], 0.0, 1.0)
-    om = pred[..., 3] * OMEGA_SCALE * U / n
-    rho = 1.0 + pred[..., 4] * U * U
-    dyux, dxux = np.gradient(ux)
-    dyuy, dxuy = np.gradient(uy)
-    sxy = 0.5 * (dxuy + dyux)
-    dxuy, dyux = sxy + 0.5 * om, sxy - 0.5 * om
-    dyphi, dxphi = np.gradient(phi)
-    grads = np.stack([dxux, dyux, dxuy, dyuy, dxphi, dyphi]).astype(np.float32)
-    f = lambda a: np.ascontiguousarray(a, np.float32)
-    return f(rho), f(ux), f(uy), f(phi), f(grads)
+def _sum_over_ranks(v: float, world: int, device) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())

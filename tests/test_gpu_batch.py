@@ -51,12 +51,16 @@ def same(a, b):
     return torch.equal(torch.nan_to_num(a, 9.0), torch.nan_to_num(b, 9.0))
 
 
+@pytest.mark.parametrize("schedule", [0, 1])
 @pytest.mark.parametrize("tiles", [(128, 1), (32, 4), (256, 1), (64, 2)])
-def test_batch_equals_single_lattice_runs(tiles):
+def test_batch_equals_single_lattice_runs(tiles, schedule):
     """45 steps in chunks of 7 (graph replays plus a direct remainder launch),
-    every field of every instance bit-identical to the single-lattice path."""
+    every field of every instance bit-identical to the single-lattice path;
+    both schedules (persistent launch, one launch per step)."""
     steps = 45
-    b = D.Batch(CFGS).set_run(tol=0.0, steps_per_launch=7).set_tiles(*tiles)
+    b = D.Batch(CFGS).set_run(tol=0.0, steps_per_launch=7).set_schedule(schedule)
+    b.set_tiles(*tiles)
+    assert b.schedule() == schedule
     for i, c in enumerate(CFGS):
         b.init(i, *start_fields(c, i))
     b.step(steps)
@@ -90,7 +94,8 @@ def test_batch_instance_matches_oracle():
         assert err < 1e-5, (k, err)
 
 
-def test_convergence_freezes_instance():
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_convergence_freezes_instance(schedule):
     """An instance whose residual drops below tol stops; its state is the one
     the single path reaches one step after the check that froze it."""
     slow = cfg(48, 48, "cavity", 0.2, check=20, u_lid=0.05)
@@ -103,7 +108,7 @@ def test_convergence_freezes_instance():
     tol = rs[10] * 1.0001
     first = next(k for k, r in enumerate(rs) if r < tol)   # checks at t = 20 (k + 1)
     t_tol = 20 * (first + 1)
-    b = D.Batch([slow, fast]).set_run(tol=tol, steps_per_launch=40)
+    b = D.Batch([slow, fast]).set_run(tol=tol, steps_per_launch=40).set_schedule(schedule)
     b.init(0, *start_fields(slow, 0)).init(1, *start_fields(fast, 0))
     b.step(600)
     st = b.stats()
@@ -121,6 +126,45 @@ def test_convergence_freezes_instance():
     assert st2["init_time"][0] == 600
     assert st2["flags"][0] == D.INST_CONVERGED and st2["steps_to_tol"][0] == t_tol
     assert st2["state_time"][0] - st2["init_time"][0] == t_tol + 1
+
+
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_instance_tolerance_and_step_limit(schedule):
+    """Per-instance run settings: the same cavity three times in one batch,
+    one frozen by its own tolerance, one by the batch's, one capped by its own
+    step limit before it converges (flag INST_CAPPED, frozen at the first
+    check at or past the limit).  The state each stops in is the single path's
+    at the same time."""
+    c = cfg(48, 48, "cavity", 0.2, check=20, u_lid=0.05)
+    ref = D.Lattice(c).init(*start_fields(c, 0))
+    rs = []
+    for _ in range(30):
+        ref.step(20)
+        rs.append(ref.stats()["residual"])
+    loose, tight = rs[5] * 1.0001, rs[20] * 1.0001
+    t_loose = 20 * (next(k for k, r in enumerate(rs) if r < loose) + 1)
+    t_tight = 20 * (next(k for k, r in enumerate(rs) if r < tight) + 1)
+    b = D.Batch([c, c, c]).set_run(tol=tight, steps_per_launch=40).set_schedule(schedule)
+    b.set_instance_run(0, tol=loose)
+    b.set_instance_run(2, tol=1e-30, max_steps=170)     # limit between two checks
+    for i in range(3):
+        b.init(i, *start_fields(c, 0))
+    b.step(800)
+    st = b.stats()
+    assert list(st["flags"]) == [D.INST_CONVERGED, D.INST_CONVERGED, D.INST_CAPPED]
+    assert st["steps_to_tol"][0] == t_loose and st["steps_to_tol"][1] == t_tight
+    assert st["steps_to_tol"][2] == -1 and st["state_time"][2] == 181   # check at t = 180
+    capped = b.fields(2)
+    again = D.Lattice(c).init(*start_fields(c, 0)).step(181).fields()
+    for k in D.FIELD_NAMES:
+        assert same(capped[k], again[k]), k
+    # settings survive a re-init; a negative tolerance returns to the batch's
+    b.set_instance_run(0, tol=-1.0)
+    b.init(0, *start_fields(c, 0)).init(2, *start_fields(c, 0))
+    b.step(800)
+    st2 = b.stats()
+    assert st2["flags"][0] == D.INST_CONVERGED and st2["steps_to_tol"][0] == t_tight
+    assert st2["flags"][2] == D.INST_CAPPED
 
 
 def test_divergence_is_isolated():
