@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="tg",
-                    choices=["tg", "sweep", "batch", "cavity", "surrogate", "gemm", "slabs"],
+                    choices=["tg", "sweep", "batch", "cavity", "surrogate", "gemm", "slabs",
+                             "conv"],
                     help="tg: Taylor-Green throughput point; sweep: Taylor-Green at N = 1024, "
                          "4096, 8192, 16384 for each storage; batch: 512 uneven cavities; "
                          "cavity: 256^2 cavities run to steady state; slabs: one lattice "
@@ -894,6 +895,93 @@ def run_gemm(args, world, rank, local):
         "device_error_word": err.value, "shapes": rows}))
 
 
+# U-Net 3x3 convolutions that take the implicit path (input channels a
+# multiple of 64), forward, at 256^2 / batch 16 (width 32): (H, W, Cin, Cout)
+CONV_SHAPES = [(256, 256, 64, 32), (128, 128, 64, 64), (128, 128, 128, 64), (128, 128, 64, 32),
+               (64, 64, 64, 128), (64, 64, 128, 128), (64, 64, 256, 128), (64, 64, 128, 64),
+               (32, 32, 128, 128)]
+
+
+def run_conv(args, world, rank, local):
+    """The surrogate's 3x3 convolutions: implicit GEMM on tcgen05 (4-D TMA
+    boxes per tap, no patch matrix) against im2col + the tcgen05 GEMM, CUDA
+    events per shape; reports the aggregate BF16 TFLOP/s of the implicit form
+    and the DRAM-free bound of each (2 P N 9 C flops)."""
+    import torch
+    from paper_1908_06742_gb300 import build as B
+    from paper_1908_06742_gb300 import ddflb as D
+    B.build()
+    torch.cuda.set_device(local)
+    lib = D.load()
+    st = torch.cuda.current_stream()
+    Bt = 16
+    rows, tot = [], {"implicit": [0.0, 0.0], "im2col": [0.0, 0.0]}
+    for H, W, C, N in CONV_SHAPES:
+        g = torch.Generator(device="cuda").manual_seed(H + C + N)
+        X = torch.randn(Bt, H, W, C, device="cuda", generator=g).to(torch.bfloat16)
+        Wt = (0.05 * torch.randn(N, 9 * C, device="cuda", generator=g)).to(torch.bfloat16)
+        Y = torch.empty(Bt * H * W, N, dtype=torch.bfloat16, device="cuda")
+        col = torch.empty(Bt * H * W, 9 * C, dtype=torch.bfloat16, device="cuda")
+        P = Bt * H * W
+
+        def implicit():
+            D._check(lib.ddflb_nn_conv3x3(X.data_ptr(), Bt, H, W, C, C, Wt.data_ptr(), N, None,
+                                          0, Y.data_ptr(), N, None, 1, 0, st.cuda_stream))
+
+        def explicit():
+            D._check(lib.ddflb_nn_im2col(X.data_ptr(), Bt, H, W, C, C, col.data_ptr(), 0,
+                                         st.cuda_stream))
+            D._check(lib.ddflb_nn_gemm(col.data_ptr(), Wt.data_ptr(), P, N, 9 * C, 9 * C, 9 * C,
+                                       None, 0, Y.data_ptr(), N, None, 1, 0, 1, None,
+                                       st.cuda_stream))
+        row = {"H": H, "W": W, "C": C, "N": N, "pixels": P}
+        fl = 2.0 * P * N * 9 * C
+        for tag, fn in (("implicit", implicit), ("im2col", explicit)):
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(args.steps):
+                fn()
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            row[f"ms_{tag}"] = round(ms, 4)
+            row[f"tflops_{tag}"] = round(fl / ms / 1e9, 1)
+            tot[tag][0] += fl
+            tot[tag][1] += ms
+        # bytes the implicit form must move at least: activation in, output out, weights
+        row["min_bytes"] = P * C * 2 + P * N * 2 + N * 9 * C * 2
+        row["gbs_implicit"] = round(row["min_bytes"] / (row["ms_implicit"] / 1e3) / 1e9, 1)
+        rows.append(row)
+        del X, Wt, Y, col
+    err = ctypes.c_int32(-1)
+    D._check(lib.ddflb_nn_take_error(ctypes.byref(err), None))
+    if rank != 0:
+        return
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak, kind = float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        peak, kind = 1900.0, "fallback"
+    agg = {k: v[0] / v[1] / 1e9 for k, v in tot.items()}
+    print(json.dumps({
+        "metric": "BF16 TFLOP/s, surrogate 3x3 convolutions (aggregate)",
+        "value": round(agg["implicit"], 1), "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot["implicit"][1], 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic",
+        "config": {"workload": "U-Net 3x3 convolutions with >= 64 input channels, 256^2 level "
+                               "sizes, batch 16, forward (BF16 out, leaky ReLU)",
+                   "kernel": "implicit GEMM, tcgen05 + 4-D TMA (ddflb_nn_conv3x3) vs im2col + "
+                             "tcgen05 GEMM"},
+        "roofline": {"bound": "tensor", "achieved": round(agg["implicit"], 1), "peak": peak,
+                     "unit": "TFLOP/s", "frac": round(agg["implicit"] / peak, 4), "peak_kind": kind},
+        "im2col_gemm_tflops": round(agg["im2col"], 1), "device_error_word": err.value,
+        "shapes": rows}))
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
@@ -911,6 +999,8 @@ def main():
         run_sweep(args, world, rank, local)
     elif args.workload == "slabs":
         run_slabs(args, world, rank, local)
+    elif args.workload == "conv":
+        run_conv(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

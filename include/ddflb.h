@@ -491,6 +491,29 @@ ddflb_status ddflb_nn_set_gemm_path(int32_t path);
 /* Copy to *error and clear the tcgen05 GEMM's device error word (1 = a bounded
  * wait ran out and a tile was skipped; 0 = none).  Synchronises `stream`. */
 ddflb_status ddflb_nn_take_error(int32_t* error, void* stream);
+/* 3x3 convolution with zero padding as an implicit GEMM on the tensor cores:
+ * Y[p][n] = act(sum over taps t and channels c of X[p + s(t)][c] Wt[n][t][c]
+ * + bias[n]), with s(t) = (t / 3 - 1, t % 3 - 1) in (y, x), X BF16 NHWC
+ * [B][H][W] with channel stride cs (C channels read, C a multiple of 64),
+ * Wt BF16 [N][9 C] (tap-major then channel, the im2col order), outputs as
+ * ddflb_nn_gemm (Cf FP32 [B H W][ldc] and/or Cb BF16 [B H W][ldcb]).  No
+ * patch matrix is formed: the TMA producer reads each tap's 128-pixel box of
+ * the activation (a 4-D tensor map over c, w, h, image; zeros outside the
+ * image) straight into the swizzled operand tile, in the same K order as
+ * im2col + ddflb_nn_gemm, whose results it reproduces bit for bit.  Needs W
+ * a divisor or a multiple of 128, the tile boxes whole (H divisible by
+ * 128 / W where W < 128; B by 128 / (H W) where H W < 128), B H W a multiple
+ * of 128, X and Wt 16-byte aligned; else EINVAL (use im2col).  Asynchronous
+ * on stream; always the tcgen05 kernel (ddflb_nn_set_gemm_path does not
+ * apply). */
+ddflb_status ddflb_nn_conv3x3(const void* X, int32_t B, int32_t H, int32_t W, int32_t C,
+                              int32_t cs, const void* Wt, int32_t N, float* Cf, int32_t ldc,
+                              void* Cb, int32_t ldcb, const float* bias, int32_t act,
+                              int32_t accumulate, void* stream);
+/* Weights of the adjoint convolution: Wf[ci][t][co] = Wt[co][8 - t][ci]
+ * (BF16, Wt [Co][9][Ci] -> Wf [Ci][9][Co]), so that dX = conv3x3(dY, Wf)
+ * with C = Co and N = Ci is the input gradient of Y = conv3x3(X, Wt). */
+ddflb_status ddflb_nn_conv3x3_flip(const void* Wt, int32_t Co, int32_t Ci, void* Wf, void* stream);
 /* 3x3 patches of X (BF16 NHWC [B][H][W][C], stride cs, zero padding):
  * col [B*H*W][9*C] (tap-major then channel), or transposed [9*C][B*H*W]. */
 ddflb_status ddflb_nn_im2col(const void* X, int32_t B, int32_t H, int32_t W, int32_t C,

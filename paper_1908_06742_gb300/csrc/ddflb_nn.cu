@@ -71,6 +71,13 @@ struct GemmArgs {
   int accumulate;  // Cf += result (FP32 only)
   int kchunk;      // K range per blockIdx.z (split-K); == K when not split
   float* partial;  // split-K: slice z written to partial + z*M*N (row-major [M][N])
+  // implicit 3x3 convolution (conv_c > 0): A is the NHWC activation seen
+  // through a 4-D tensor map, row m of the product = pixel m, and k-step kt
+  // reads tap kt / (conv_c / 64) (dy = tap / 3 - 1, dx = tap % 3 - 1) of the
+  // 64-channel chunk kt % (conv_c / 64); a tile of 128 pixels is one box of
+  // conv_bw x conv_bh x conv_bb (w, h, image)
+  int conv_c, conv_w, conv_h;
+  int conv_bw, conv_bh, conv_bb;
 };
 
 __global__ void __launch_bounds__(256) k_gemm(GemmArgs g) {
@@ -253,6 +260,17 @@ __device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap* map, int
       "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
       " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// one 4-D TMA box (c, w, h, image) into shared memory, counted on `bar`; the
+// w and h coordinates may lie outside the image (the box reads zeros there)
+__device__ __forceinline__ void tma_4d(uint32_t dst, const CUtensorMap* map, int c, int w, int h,
+                                       int b, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c), "r"(w), "r"(h), "r"(b), "r"(bar)
       : "memory");
 }
 
@@ -584,7 +602,15 @@ __global__ void __launch_bounds__(tcp::THREADS, 1) k_gemm_tcp(
                        : "memory");
           const uint32_t sa = tiles_u + st * C::STAGE;
           const int k0 = kbeg + kt * tc::BK;  // a multiple of 64 elements (128 B)
-          tma_2d(sa, &tmA, k0, m0, bar);
+          if (g.conv_c) {
+            // implicit convolution: the tap's shifted box of 128 pixels
+            const int cpt = g.conv_c >> 6, tap = kt / cpt, c0 = (kt - tap * cpt) << 6;
+            const int hw = g.conv_h * g.conv_w, b0 = m0 / hw, rem = m0 - b0 * hw;
+            const int h0 = rem / g.conv_w, w0 = rem - h0 * g.conv_w;
+            tma_4d(sa, &tmA, c0, w0 + tap % 3 - 1, h0 + tap / 3 - 1, b0, bar);
+          } else {
+            tma_2d(sa, &tmA, k0, m0, bar);
+          }
           tma_2d(sa + T::A_TILE, &tmB, k0, n0, bar);
         }
       }
@@ -853,6 +879,18 @@ __global__ void k_col2im(const float* __restrict__ dcol, int B, int H, int W, in
 }
 
 // dst[n][m] = src[m][n] (BF16, src row stride lds)
+// Wf[ci][tap][co] = Wt[co][8 - tap][ci]: the weights of the adjoint of a 3x3
+// convolution (dX = conv3x3(dY, Wf) with the taps mirrored and the channel
+// roles swapped)
+__global__ void k_conv_flip(const bf16* __restrict__ Wt, int Co, int Ci, bf16* __restrict__ Wf) {
+  const int64_t n = (int64_t)Co * 9 * Ci;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int ci = (int)(i % Ci), tap = (int)((i / Ci) % 9), co = (int)(i / (9 * (int64_t)Ci));
+    Wf[((int64_t)ci * 9 + (8 - tap)) * Co + co] = Wt[i];
+  }
+}
+
 __global__ void k_transpose(const bf16* __restrict__ src, int M, int N, int lds,
                             bf16* __restrict__ dst) {
   __shared__ bf16 t[32][33];
@@ -1115,6 +1153,23 @@ bool make_map(CUtensorMap* m, const void* base, int rows, int K, int ld, int box
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// 4-D map over an NHWC BF16 activation [B][H][W][cs] (C channels used): boxes
+// of 64 channels x bw x bh x bb pixels, 128-byte swizzle, zero fill outside the
+// image (the convolution's padding)
+bool make_map_conv(CUtensorMap* m, const void* base, int B, int H, int W, int C, int cs, int bw,
+                   int bh, int bb) {
+  EncodeTiled fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+  const cuuint64_t strides[3] = {(cuuint64_t)cs * 2, (cuuint64_t)W * cs * 2,
+                                 (cuuint64_t)H * W * cs * 2};
+  const cuuint32_t box[4] = {64, (cuuint32_t)bw, (cuuint32_t)bh, (cuuint32_t)bb};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int sm_count() {
   static int n = 0;
   if (!n) {
@@ -1142,6 +1197,28 @@ ddflb_status gemm_tcp_bn(const GemmArgs& g, int tm, int tn, int tz, cudaStream_t
   const int grid = ntiles < sm_count() ? ntiles : sm_count();
   k_gemm_tcp<BN><<<grid, tcp::THREADS, tcp::Cfg<BN>::SMEM, s>>>(ma, mb, g, tm, tn, tz);
   return launched("gemm tcgen05 persistent");
+}
+
+// Implicit 3x3 convolution on the persistent kernel: the A map is 4-D over the
+// activation, the B map 2-D over the weights [N][9 C].
+template <int BN>
+ddflb_status conv_tcp_bn(const GemmArgs& g, const void* X, int B, int cs, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_gemm_tcp<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             tcp::Cfg<BN>::SMEM) != cudaSuccess)
+      return launched("conv tcgen05 attribute");
+    attr = true;
+  }
+  CUtensorMap ma, mb;
+  if (!make_map_conv(&ma, X, B, g.conv_h, g.conv_w, g.conv_c, cs, g.conv_bw, g.conv_bh,
+                     g.conv_bb) ||
+      !make_map(&mb, g.B, g.N, g.K, g.ldb, BN))
+    return bad("conv3x3: TMA tensor map encoding failed");
+  const int tm = g.M / tc::BM, tn = (g.N + BN - 1) / BN;
+  const int grid = tm * tn < sm_count() ? tm * tn : sm_count();
+  k_gemm_tcp<BN><<<grid, tcp::THREADS, tcp::Cfg<BN>::SMEM, s>>>(ma, mb, g, tm, tn, 1);
+  return launched("conv3x3 tcgen05");
 }
 
 template <int BN>
@@ -1252,6 +1329,63 @@ ddflb_status ddflb_nn_gemm(const void* A, const void* B, int32_t M, int32_t N, i
   k_splitk_reduce<<<grid_for((int64_t)M * N), 256, 0, s>>>(partial, z, M, N, Cf, ldc, bias, act,
                                                            accumulate);
   return launched("gemm split-K");
+}
+
+ddflb_status ddflb_nn_conv3x3(const void* X, int32_t B, int32_t H, int32_t W, int32_t C,
+                              int32_t cs, const void* Wt, int32_t N, float* Cf, int32_t ldc,
+                              void* Cb, int32_t ldcb, const float* bias, int32_t act,
+                              int32_t accumulate, void* stream) {
+  if (!X || !Wt || B <= 0 || H <= 0 || W <= 0 || N <= 0 || (!Cf && !Cb))
+    return bad("conv3x3: bad arguments");
+  if (C % 64 || cs < C || cs % 8 || ((uintptr_t)X % 16) || ((uintptr_t)Wt % 16))
+    return bad("conv3x3: C must be a multiple of 64, cs a multiple of 8 (>= C), X and Wt "
+               "16-byte aligned");
+  if ((Cf && ldc < N) || (Cb && ldcb < N)) return bad("conv3x3: leading dims");
+  if (act < 0 || act > 1) return bad("conv3x3: act must be 0 (none) or 1 (leaky ReLU)");
+  // a tile of 128 consecutive pixels must be one box (w, h, image)
+  const int bw = W < 128 ? W : 128;
+  const int bh = 128 / bw < H ? 128 / bw : H;
+  const int bb = 128 / (bw * bh);
+  if (128 % bw || (W >= 128 && W % 128) || H % bh || bw * bh * bb != 128 || B % bb ||
+      ((int64_t)B * H * W) % 128 || (int64_t)B * H * W > INT32_MAX)
+    return bad("conv3x3: 128-pixel tiles need W a divisor of 128 or a multiple of it, and whole "
+               "boxes of rows and images");
+  GemmArgs g{};
+  g.A = (const bf16*)X;
+  g.B = (const bf16*)Wt;
+  g.M = B * H * W;
+  g.N = N;
+  g.K = 9 * C;
+  g.lda = 9 * C;
+  g.ldb = 9 * C;
+  g.Cf = Cf;
+  g.Cb = (bf16*)Cb;
+  g.ldc = ldc;
+  g.ldcb = ldcb;
+  g.bias = bias;
+  g.act = act;
+  g.accumulate = accumulate;
+  g.kchunk = g.K;
+  g.partial = nullptr;
+  g.conv_c = C;
+  g.conv_w = W;
+  g.conv_h = H;
+  g.conv_bw = bw;
+  g.conv_bh = bh;
+  g.conv_bb = bb;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int bn = N <= 32 ? 32 : N <= 64 ? 64 : 128;
+  return bn == 32 ? conv_tcp_bn<32>(g, X, B, cs, s)
+         : bn == 64 ? conv_tcp_bn<64>(g, X, B, cs, s)
+                    : conv_tcp_bn<128>(g, X, B, cs, s);
+}
+
+ddflb_status ddflb_nn_conv3x3_flip(const void* Wt, int32_t Co, int32_t Ci, void* Wf,
+                                   void* stream) {
+  if (!Wt || !Wf || Co <= 0 || Ci <= 0) return bad("conv3x3_flip: bad arguments");
+  const int64_t n = (int64_t)Co * 9 * Ci;
+  k_conv_flip<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>((const bf16*)Wt, Co, Ci, (bf16*)Wf);
+  return launched("conv3x3_flip");
 }
 
 ddflb_status ddflb_nn_im2col(const void* X, int32_t B, int32_t H, int32_t W, int32_t C,

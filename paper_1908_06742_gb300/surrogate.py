@@ -59,10 +59,14 @@ class _V:
 
 
 class UNet:
-    def __init__(self, c=32, batch=16, H=128, W=128, device="cuda", seed=0, stream=None):
+    def __init__(self, c=32, batch=16, H=128, W=128, device="cuda", seed=0, stream=None,
+                 implicit=True):
         import torch
         assert H % 8 == 0 and W % 8 == 0
         self.torch = torch
+        # 3x3 convolutions with >= 64 input channels as implicit GEMMs (no
+        # patch matrix); the others through im2col + GEMM
+        self.implicit = implicit
         self.c, self.B, self.H, self.W = c, batch, H, W
         self.dev = torch.device(device)
         self.lib = D.load()
@@ -155,11 +159,28 @@ class UNet:
         s = max(1, min(self.splits_max, 304 // max(tiles, 1), K // 2048))
         return s
 
+    def _implicit_ok(self, C, H, W):
+        """ddflb_nn_conv3x3 takes this layer (C a multiple of 64; 128-pixel
+        tiles that are whole boxes of rows and images); else im2col + GEMM."""
+        if not self.implicit or C % 64 or (self.B * H * W) % 128:
+            return False
+        bw = min(W, 128)
+        bh = min(H, 128 // bw)
+        bb = 128 // (bw * bh)
+        return (128 % bw == 0 and (W < 128 or W % 128 == 0) and H % bh == 0
+                and bw * bh * bb == 128 and self.B % bb == 0)
+
     def _conv_fwd(self, name, lv, vin, vout):
         p = self.p[name]
         H, W = self.L[lv]
         P, ci, co = self.B * H * W, p["ci"], p["co"]
         assert vin.C == ci and vout.C == co
+        if self._implicit_ok(ci, H, W):
+            # implicit GEMM: the taps are read from the activation, no patch matrix
+            _ck(self.lib.ddflb_nn_conv3x3(vin.ptr, self.B, H, W, ci, vin.cs, p["wb"].data_ptr(),
+                                          co, None, 0, vout.ptr, vout.cs, p["b"].data_ptr(),
+                                          LEAKY, 0, self.s))
+            return
         _ck(self.lib.ddflb_nn_im2col(vin.ptr, self.B, H, W, ci, vin.cs, self.col.data_ptr(), 0,
                                      self.s))
         self._gemm(self.col.data_ptr(), p["wb"].data_ptr(), P, co, 9 * ci, 9 * ci, 9 * ci,
@@ -181,6 +202,13 @@ class UNet:
         self._gemm(gbT, self.colT.data_ptr(), co, 9 * ci, P, P, P, Cf=p["gw"].data_ptr(),
                    ldc=9 * ci, splits=self._splits(co, 9 * ci, P))
         if gin is None:
+            return
+        if self._implicit_ok(co, H, W):
+            # dX = conv3x3(g, W with the taps mirrored and the channels swapped)
+            _ck(self.lib.ddflb_nn_conv3x3_flip(p["wb"].data_ptr(), co, ci, p["wT"].data_ptr(),
+                                               self.s))
+            _ck(self.lib.ddflb_nn_conv3x3(gbf, self.B, H, W, co, co, p["wT"].data_ptr(), ci,
+                                          gin.ptr, gin.cs, None, 0, None, 0, 0, self.s))
             return
         # dX = col2im(g . W)
         _ck(self.lib.ddflb_nn_transpose(p["wb"].data_ptr(), co, 9 * ci, 9 * ci,

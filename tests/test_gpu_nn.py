@@ -223,3 +223,115 @@ def test_bias_grad_column_sums(rows, C, cs):
     want = G.double().cpu().numpy()[:, :C].sum(axis=0)
     np.testing.assert_allclose(db.double().cpu().numpy(), want, rtol=0,
                                atol=1e-5 * np.sqrt(rows))
+
+
+# --------------------------------------------------------------- implicit 3x3 convolution
+def _conv_ref(X, Wt, B, H, Wd, C, cs, N, bias, act, s):
+    """im2col + the tcgen05 GEMM: the path the implicit convolution replaces."""
+    lib = D.load()
+    col = torch.empty(B * H * Wd, 9 * C, dtype=torch.bfloat16, device="cuda")
+    D._check(lib.ddflb_nn_im2col(X.data_ptr(), B, H, Wd, C, cs, col.data_ptr(), 0, s))
+    Yf = torch.empty(B * H * Wd, N, device="cuda")
+    Yb = torch.empty(B * H * Wd, N, dtype=torch.bfloat16, device="cuda")
+    D._check(lib.ddflb_nn_gemm(col.data_ptr(), Wt.data_ptr(), B * H * Wd, N, 9 * C, 9 * C, 9 * C,
+                               Yf.data_ptr(), N, Yb.data_ptr(), N,
+                               None if bias is None else bias.data_ptr(), act, 0, 1, None, s))
+    return Yf, Yb
+
+
+@pytest.mark.parametrize("B,H,Wd,C,cs,off,N,act", [
+    (2, 16, 16, 64, 64, 0, 32, 1), (16, 8, 8, 128, 192, 64, 128, 0), (1, 4, 256, 64, 72, 8, 64, 1),
+    (4, 32, 32, 64, 128, 64, 96, 1), (16, 64, 64, 64, 64, 0, 64, 0)])
+def test_conv3x3_equals_im2col_gemm(B, H, Wd, C, cs, off, N, act):
+    """The implicit convolution (4-D TMA boxes per tap, zero padding from the
+    tensor map) against im2col + GEMM on the same BF16 data, bit for bit:
+    boxes of one row segment (W = 256), whole rows (W = 16, 32, 64) and two
+    images (8 x 8), channel-strided input read from a channel offset of a
+    wider buffer, N below, at and between tile widths, bias and activation."""
+    g = torch.Generator().manual_seed(B * H + C + N)
+    buf = torch.randn(B, H, Wd, cs, generator=g).to(torch.bfloat16).cuda()
+    X = buf[..., off:]                     # channels [off, off + C) of the buffer, stride cs
+    Xc = X[..., :C].contiguous().view(-1)  # only for the reference's im2col (stride C)
+    Wt = (0.1 * torch.randn(N, 9 * C, generator=g)).to(torch.bfloat16).cuda()
+    bias = torch.randn(N, generator=g).cuda()
+    s = torch.cuda.current_stream().cuda_stream
+    lib = D.load()
+    Yf = torch.full((B * H * Wd, N), 7.0, device="cuda")
+    Yb = torch.empty(B * H * Wd, N, dtype=torch.bfloat16, device="cuda")
+    D._check(lib.ddflb_nn_conv3x3(X.data_ptr(), B, H, Wd, C, cs, Wt.data_ptr(), N, Yf.data_ptr(),
+                                  N, Yb.data_ptr(), N, bias.data_ptr(), act, 0, s))
+    Rf, Rb = _conv_ref(Xc, Wt, B, H, Wd, C, C, N, bias, act, s)
+    torch.cuda.synchronize()
+    assert take_error() == 0
+    assert torch.equal(Yf, Rf) and torch.equal(Yb, Rb)
+
+
+def test_conv3x3_flip_gives_the_input_gradient():
+    """dX = conv3x3(dY, flip(W)) equals the im2col path's input gradient
+    (GEMM dY . W into patch columns, then col2im), up to the order of the FP32
+    additions (the implicit form sums all 9 taps and channels in one
+    accumulator)."""
+    B, H, Wd, Ci, Co = 4, 32, 32, 64, 128
+    g = torch.Generator().manual_seed(11)
+    dY = torch.randn(B, H, Wd, Co, generator=g).to(torch.bfloat16).cuda()
+    Wt = (0.1 * torch.randn(Co, 9 * Ci, generator=g)).to(torch.bfloat16).cuda()
+    s = torch.cuda.current_stream().cuda_stream
+    lib = D.load()
+    Wf = torch.empty(Ci, 9 * Co, dtype=torch.bfloat16, device="cuda")
+    D._check(lib.ddflb_nn_conv3x3_flip(Wt.data_ptr(), Co, Ci, Wf.data_ptr(), s))
+    dX = torch.empty(B * H * Wd, Ci, device="cuda")
+    D._check(lib.ddflb_nn_conv3x3(dY.data_ptr(), B, H, Wd, Co, Co, Wf.data_ptr(), Ci,
+                                  dX.data_ptr(), Ci, None, 0, None, 0, 0, s))
+    # reference: dcol = dY . W  ([P][Co] x [Co][9 Ci]), then the col2im adjoint
+    WT = Wt.t().contiguous()                                 # [9 Ci][Co]
+    dcol = torch.empty(B * H * Wd, 9 * Ci, device="cuda")
+    D._check(lib.ddflb_nn_gemm(dY.data_ptr(), WT.data_ptr(), B * H * Wd, 9 * Ci, Co, Co, Co,
+                               dcol.data_ptr(), 9 * Ci, None, 0, None, 0, 0, 1, None, s))
+    ref = torch.empty(B * H * Wd, Ci, device="cuda")
+    D._check(lib.ddflb_nn_col2im(dcol.data_ptr(), B, H, Wd, Ci, ref.data_ptr(), Ci, s))
+    torch.cuda.synchronize()
+    assert take_error() == 0
+    d = (dX - ref).abs().max().item()
+    assert d <= 1e-5 * ref.abs().max().item(), d
+
+
+def test_conv3x3_rejects_unsupported_shapes():
+    lib = D.load()
+    x = torch.zeros(2, 8, 8, 64, dtype=torch.bfloat16, device="cuda")
+    w = torch.zeros(32, 9 * 64, dtype=torch.bfloat16, device="cuda")
+    y = torch.empty(128, 32, device="cuda")
+    with pytest.raises(D.DdflbError, match="multiple of 64"):
+        D._check(lib.ddflb_nn_conv3x3(x.data_ptr(), 2, 8, 8, 32, 64, w.data_ptr(), 32,
+                                      y.data_ptr(), 32, None, 0, None, 0, 0, None))
+    with pytest.raises(D.DdflbError, match="128-pixel tiles"):
+        D._check(lib.ddflb_nn_conv3x3(x.data_ptr(), 2, 8, 6, 64, 64, w.data_ptr(), 32,
+                                      y.data_ptr(), 32, None, 0, None, 0, 0, None))
+
+
+def test_unet_implicit_conv_matches_im2col_path_and_oracle():
+    """The U-Net with its 3x3 convolutions of >= 64 input channels as implicit
+    GEMMs (forward and input gradient): the forward pass is bit-identical to
+    the im2col + GEMM network, every gradient agrees with it up to the order
+    of FP32 additions (1e-3) and with the FP64 network oracle within the BF16
+    bound of the other test (width 32, so levels 1-3 use the implicit path)."""
+    nets = []
+    for implicit in (True, False):
+        net, xb, t = make_net(c=32, batch=4, H=32, seed=3)
+        net.implicit = implicit
+        out = net.forward(xb).clone()
+        loss = net.backward(t)
+        torch.cuda.synchronize()
+        nets.append((net, out, float(loss.item()), net.grads()))
+    (ni, oi, li, gi), (ne, oe, le, ge) = nets
+    assert sum(ni._implicit_ok(ci, *ni.L[lv]) for (n, lv, *_), (_, ci, _) in
+               zip(ni.layers, ni.specs)) >= 6            # the implicit path is in use
+    assert torch.equal(oi, oe) and li == le
+    for name, _, _ in ni.specs:
+        for k in (0, 1):
+            assert rel(gi[name][k], ge[name][k]) < 1e-3, (name, k, rel(gi[name][k], ge[name][k]))
+    P = oracle_params(ni)
+    ref_out, cache = OU.forward(P, xb.double().cpu().numpy())
+    G = OU.backward(P, cache, ref_out, t.double().cpu().numpy())
+    worst = max(rel(gi[name][k], G[name][k]) for name, _, _ in ni.specs for k in (0, 1))
+    print("implicit U-Net: worst gradient error against the oracle", worst)
+    assert rel(oi.double().cpu().numpy(), ref_out) < 2e-2 and worst < 6e-2
