@@ -54,6 +54,10 @@ def parse():
                          "cavity: 256^2 cavities run to steady state; slabs: one lattice "
                          "divided into y-slabs, one per rank, halos exchanged every step")
     ap.add_argument("--instances", type=int, default=512)
+    ap.add_argument("--schedule", default="auto", choices=["auto", "0", "1"],
+                    help="batch: launch schedule (0 persistent, 1 one launch per step; auto: "
+                         "the autotuner's choice over both)")
+    ap.add_argument("--tiles", default="64x4", help="batch tile shape when --schedule is not auto")
     ap.add_argument("--boot", type=int, default=0,
                     help="surrogate: training draws run from rest before a first network "
                          "warm-starts the remaining ones (0: all from rest)")
@@ -455,7 +459,12 @@ def run_batch(args, world, rank, local):
     with torch.cuda.stream(stream):
         b = D.Batch(cfgs, device=dev, stream=stream)
         b.set_run(tol=0.0, steps_per_launch=lb)
-        _, tune = b.autotune(trial_steps=20, cache=False)
+        if args.schedule == "auto":
+            _, tune = b.autotune(trial_steps=20, cache=False)
+        else:
+            tx, ty = (int(v) for v in args.tiles.split("x"))
+            b.set_schedule(int(args.schedule)).set_tiles(tx, ty)
+            tune = {"choice": list(b.tiles()) + [b.schedule()], "forced": True}
         starts = [inputs.rest(c.nx, c.ny, phi=0.0) for c in cfgs]
         for i, F in enumerate(starts):
             b.init(i, F.rho, F.ux, F.uy, F.phi)
@@ -518,7 +527,8 @@ def run_batch(args, world, rank, local):
                    "cells": int(job_cells), "cells_rank0": cells, "tiles": tune,
                    "l2": f"{288 * cells / 1e9:.1f} GB of populations on rank 0"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "peak_kind": kind, "kernel": "k_batch",
+                     "frac": round(achieved / peak, 4), "peak_kind": kind,
+                     "kernel": "k_batch" if tune["choice"][3] == 0 else "k_batch_tile",
                      # bytes per node-step from a 64-cavity capture, times this launch's
                      # node-steps (traffic grows in proportion: every node-step moves the
                      # same 18 planes)
