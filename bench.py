@@ -293,6 +293,21 @@ def traffic_record(key, n_units):
         return None
 
 
+def traffic_source(key, units):
+    """Where the traffic figure comes from: the ncu capture recorded under key,
+    per cell, scaled to this launch."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            e = json.load(f).get(key)
+    except Exception:
+        e = None
+    if not e:
+        return None
+    return (f"ncu dram__bytes_read.sum + dram__bytes_write.sum per cell on {e['measured_on']}; "
+            f"x {units} (traffic grows in proportion to the cells a launch updates)")
+
+
 def run_ours(args, world, rank, local):
     import torch
     from paper_1908_06742_gb300 import build as B
@@ -408,7 +423,11 @@ def run_ours(args, world, rank, local):
                      "frac": round(achieved / peak, 4), "peak_kind": kind,
                      "kernel": step_kernel_name(args),
                      "algorithmic_bytes_per_launch": algo_bytes,
-                     "traffic": traffic_per_launch(args, cells)},
+                     "traffic": traffic_per_launch(args, cells),
+                     "traffic_source": traffic_source(step_kernel_name(args) + "_" + args.storage
+                                                      + ("" if args.scalar_model == "mrt"
+                                                         else "_" + args.scalar_model),
+                                                      "cells of this launch")},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,
@@ -533,9 +552,13 @@ def run_batch(args, world, rank, local):
                      # node-steps (traffic grows in proportion: every node-step moves the
                      # same 18 planes)
                      "algorithmic_bytes_per_launch": 144 * cells * lb,
-                     "traffic": traffic_record("k_batch_fp32", cells * lb)},
+                     "traffic": traffic_record("k_batch_fp32", cells * lb),
+                     "traffic_source": traffic_source("k_batch_fp32", "node-steps of this launch")},
         "cpu_baseline": None, "e2e": e2e,
-        "gpu_launches": args.steps,
+        # schedule 0: one cooperative launch per chunk of lb steps; schedule 1: per
+        # step the node kernel, the sums kernel and the check kernel, then the
+        # state-time update
+        "gpu_launches": args.steps * (1 if tune["choice"][3] == 0 else 3 * lb + 1),
         "clocks": clk,
         "checks": {"flags_nonzero": int(sum(f != 0 for f in flags)), "instances": len(flags),
                    "status": int(st["status"])},
