@@ -617,6 +617,32 @@ __device__ __forceinline__ void collide(const LbParams& P, int x, int y, float d
   }
 }
 
+// The unforced MRT collision of one node on populations held in storage units
+// (the deviations times the power-of-two storage scales sf, sg of the 16-bit
+// formats), without converting each population: the moments are linear, so
+// those of the scaled populations are the scaled moments; only the density and
+// momentum are brought back to physical units for rho and u, and the
+// equilibrium products take sf rho (flow) and sg phi (scalar) in place of rho
+// and phi.  Scaling by a power of two commutes with rounding (every sum,
+// product and fused multiply-add of scaled operands rounds to exactly the
+// scaled result), so this is bit-identical to collide<false, 0> on d / s
+// followed by the storage conversion of d s, with 6 multiplies instead of 36.
+__device__ __forceinline__ void collide_scaled(const LbParams& P, float df[9], float dg[9]) {
+  const Mom mf = moments_flow(df), mg = moments_scalar(dg);
+  Mom fu = mf;  // flow moments in physical units where the scalar lattice needs them
+  fu.k0 = mf.k0 * P.isf;
+  fu.kx = mf.kx * P.isf;
+  fu.ky = mf.ky * P.isf;
+  Mom gu = mg;
+  gu.k0 = mg.k0 * P.isg;
+  const Macro q = macro(P, fu, gu);
+  Macro qf = q, qg = q;
+  qf.rho = q.rho * P.sf;
+  qg.phi = q.phi * P.sg;
+  relax(P.wf, neq_flow(mf, qf), df);
+  relax(P.wg, neq_scalar(P, mg, fu, qg), dg);
+}
+
 // Macroscopic state and the non-equilibrium moments the kinematics use.  With
 // a force the flow moments are those of f = f-bar + S/2 (the distribution whose
 // non-equilibrium part Sec. 4 relates to the velocity gradients).  The odd

@@ -186,12 +186,13 @@ template <> __device__ __forceinline__ float half_of<__nv_bfloat16>(unsigned w, 
 template <typename S> __device__ __forceinline__ float elem(uint2 v, int k) {
   return half_of<S>(k < 2 ? v.x : v.y, k & 1);
 }
-template <typename S> __device__ __forceinline__ unsigned bits_of(float v, float s);
-template <> __device__ __forceinline__ unsigned bits_of<__half>(float v, float s) {
-  return __half_as_ushort(__float2half_rn(v * s));
+// storage bits of a value already in storage units
+template <typename S> __device__ __forceinline__ unsigned bits_of(float v);
+template <> __device__ __forceinline__ unsigned bits_of<__half>(float v) {
+  return __half_as_ushort(__float2half_rn(v));
 }
-template <> __device__ __forceinline__ unsigned bits_of<__nv_bfloat16>(float v, float s) {
-  return __bfloat16_as_ushort(__float2bfloat16_rn(v * s));
+template <> __device__ __forceinline__ unsigned bits_of<__nv_bfloat16>(float v) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn(v));
 }
 
 template <typename S, int BC>
@@ -251,21 +252,18 @@ __global__ void __launch_bounds__(128) k_step_quad(LbParams P, const S* __restri
   unsigned fw[9][2], gw[9][2];  // packed results: [plane][low / high word]
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    float df[9], dg[9];
+    float df[9], dg[9];  // in storage units (scaled deviations)
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
       // node x0 + k pulls element k - e_ax of the own group (or the neighbour's)
       const int e = k - EX[a];
-      df[a] = (e < 0 || e > 3 ? fe[a] : elem<S>(fo[a], e)) * P.isf;
-      dg[a] = (e < 0 || e > 3 ? ge[a] : elem<S>(go[a], e)) * P.isg;
+      df[a] = e < 0 || e > 3 ? fe[a] : elem<S>(fo[a], e);
+      dg[a] = e < 0 || e > 3 ? ge[a] : elem<S>(go[a], e);
     }
-    const Mom mf = moments_flow(df), mg = moments_scalar(dg);
-    const Macro q = macro(P, mf, mg);
-    relax(P.wf, neq_flow(mf, q), df);
-    relax(P.wg, neq_scalar(P, mg, mf, q), dg);
+    collide_scaled(P, df, dg);
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-      const unsigned bf = bits_of<S>(df[a], P.sf), bg = bits_of<S>(dg[a], P.sg);
+      const unsigned bf = bits_of<S>(df[a]), bg = bits_of<S>(dg[a]);
       if (k & 1) {
         fw[a][k >> 1] |= bf << 16;
         gw[a][k >> 1] |= bg << 16;

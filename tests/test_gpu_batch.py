@@ -78,6 +78,28 @@ def test_batch_equals_single_lattice_runs(tiles, schedule):
         assert math.isclose(st["residual"][i], r, rel_tol=1e-12), (i, st["residual"][i], r)
 
 
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_many_tiles_per_cta(schedule):
+    """One CTA per SM and a 300 x 200 cavity added: the persistent launch's
+    CTAs each walk a range of tiles that crosses instances (parameters
+    restaged at every change), still bit-identical to the single-lattice path;
+    the per-step schedule runs the same tiles one per CTA."""
+    cfgs = CFGS + [cfg(300, 200, "cavity", 0.03, u_lid=0.1, phi_lid=1.0, phi_wall=0.0)]
+    steps = 23
+    b = D.Batch(cfgs).set_run(tol=0.0, steps_per_launch=5).set_schedule(schedule)
+    b.set_tiles(32, 4, 1)
+    for i, c in enumerate(cfgs):
+        b.init(i, *start_fields(c, i))
+    b.step(steps)
+    st = b.stats()
+    assert st["status"] == D.OK and not st["flags"].any()
+    for i, c in enumerate(cfgs):
+        ref = D.Lattice(c).init(*start_fields(c, i)).step(steps).fields()
+        got = b.fields(i)
+        for k in D.FIELD_NAMES:
+            assert same(got[k], ref[k]), (i, k)
+
+
 def test_batch_instance_matches_oracle():
     c = CFGS[3]
     b = D.Batch([c]).set_run(steps_per_launch=50)
