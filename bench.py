@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--boot", type=int, default=0,
                     help="surrogate: training draws run from rest before a first network "
                          "warm-starts the remaining ones (0: all from rest)")
+    ap.add_argument("--conv-path", type=int, default=0, choices=[0, 1],
+                    help="conv workload: 0 halo bands where W is a multiple of 128, 1 one box "
+                         "per tap everywhere")
     ap.add_argument("--gemm-shape", default=None,
                     help="gemm workload: one M,N,K,splits shape instead of the U-Net set")
     return ap.parse_args()
@@ -946,6 +949,7 @@ def run_conv(args, world, rank, local):
     B.build()
     torch.cuda.set_device(local)
     lib = D.load()
+    D._check(lib.ddflb_nn_set_conv_path(args.conv_path))
     st = torch.cuda.current_stream()
     Bt = 16
     rows, tot = [], {"implicit": [0.0, 0.0], "im2col": [0.0, 0.0]}
@@ -999,6 +1003,17 @@ def run_conv(args, world, rank, local):
     except Exception:
         peak, kind = 1900.0, "fallback"
     agg = {k: v[0] / v[1] / 1e9 for k, v in tot.items()}
+    # per shape, the roofline time: the larger of the tensor time at the BF16
+    # peak and the HBM time of the compulsory bytes at the measured copy peak
+    hbm, hbm_kind = peaks()
+    t_roof = 0.0
+    for r in rows:
+        fl = 2.0 * r["pixels"] * r["N"] * 9 * r["C"]
+        t = max(fl / (peak * 1e12), r["min_bytes"] / (hbm * 1e9)) * 1e3
+        r["roofline_ms"] = round(t, 4)
+        r["bound"] = "hbm" if r["min_bytes"] / (hbm * 1e9) * 1e12 > fl / peak else "tensor"
+        r["frac_of_roofline"] = round(t / r["ms_implicit"], 3)
+        t_roof += t
     print(json.dumps({
         "metric": "BF16 TFLOP/s, surrogate 3x3 convolutions (aggregate)",
         "value": round(agg["implicit"], 1), "unit": "TFLOP/s", "n_gpus": world,
@@ -1010,7 +1025,12 @@ def run_conv(args, world, rank, local):
                    "kernel": "implicit GEMM, tcgen05 + 4-D TMA (ddflb_nn_conv3x3) vs im2col + "
                              "tcgen05 GEMM"},
         "roofline": {"bound": "tensor", "achieved": round(agg["implicit"], 1), "peak": peak,
-                     "unit": "TFLOP/s", "frac": round(agg["implicit"] / peak, 4), "peak_kind": kind},
+                     "unit": "TFLOP/s", "frac": round(agg["implicit"] / peak, 4), "peak_kind": kind,
+                     # the layers' own roofline: sum over shapes of max(tensor time, HBM
+                     # time of the compulsory bytes) against the measured total
+                     "frac_of_layer_roofline": round(t_roof / tot["implicit"][1], 4),
+                     "hbm_peak_gbs": hbm, "hbm_peak_kind": hbm_kind},
+        "conv_path": args.conv_path,
         "im2col_gemm_tflops": round(agg["im2col"], 1), "device_error_word": err.value,
         "shapes": rows}))
 

@@ -78,6 +78,12 @@ struct GemmArgs {
   // conv_bw x conv_bh x conv_bb (w, h, image)
   int conv_c, conv_w, conv_h;
   int conv_bw, conv_bh, conv_bb;
+  // band mode (W a multiple of 128, tiles = 128-pixel row segments): the A map
+  // reads bands of 130 pixels (the segment and one halo pixel each side) of one
+  // input row; conv_ag = band-group slots (one group = the bands of all
+  // channel chunks of one input row), conv_bs = slots of the B ring, or 0 when
+  // the whole weight matrix stays resident in shared memory (N <= BN)
+  int conv_ag, conv_bs;
 };
 
 __global__ void __launch_bounds__(256) k_gemm(GemmArgs g) {
@@ -229,18 +235,24 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr, uint32_t sbo)
          ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
 // bounded wait for the completion of the mbarrier phase with the given parity
+// (the timer is read only once the phase is found incomplete)
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
   const uint64_t deadline = globaltimer_ns() + 1000000000ull;
   for (uint32_t it = 0; it < (1u << 24); ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
+    if (mbar_try(bar, parity)) return true;
     if ((it & 255) == 255 && globaltimer_ns() > deadline) return false;
   }
   return false;
@@ -494,11 +506,19 @@ __global__ void __launch_bounds__(tc::THREADS) k_gemm_tc(const __grid_constant__
 // (bounded), frees its tensor memory and returns.
 namespace tcp {
 constexpr int THREADS = 192;
+// band mode: 130 rows of 128 B (64 channels) per band, each band in its own
+// 1024-byte aligned slot (the 128-byte swizzle repeats every 8 rows)
+constexpr int BAND_ROWS = 130;
+constexpr int BAND_BYTES = BAND_ROWS * 128;
+constexpr int BAND_SLOT = 17 * 1024;
+constexpr int SMEM_MAX = 226 * 1024;  // dynamic; the 227 KB per-block limit includes static
 template <int BN>
 struct Cfg {
   using T = tc::Cfg<BN>;
-  static constexpr int STAGES = T::STAGES;
   static constexpr int STAGE = T::STAGE;
+  // one CTA per SM: a ring of about 200 KB (10, 8, 6 slots for BN = 32, 64,
+  // 128) keeps enough loads in flight to cover the L2 latency of narrow tiles
+  static constexpr int STAGES = (200 * 1024) / STAGE;
   static constexpr int SMEM = STAGES * STAGE + 1024 + 512;
   static constexpr uint32_t COLS = 2 * BN < 32 ? 32 : 2 * BN;  // two accumulators
 };
@@ -507,38 +527,45 @@ struct Cfg {
 // bounded wait that also gives up once *abort is set
 __device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, uint32_t parity,
                                              const volatile int* abort) {
+  if (mbar_try(bar, parity)) return true;
   const uint64_t deadline = globaltimer_ns() + 1000000000ull;
   for (uint32_t it = 0; it < (1u << 24); ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
+    if (mbar_try(bar, parity)) return true;
     if ((it & 255) == 255 && (*abort || globaltimer_ns() > deadline)) return false;
   }
   return false;
 }
 
-template <int BN>
+template <int BN, bool BAND = false>
 __global__ void __launch_bounds__(tcp::THREADS, 1) k_gemm_tcp(
     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmArgs g,
     int tiles_m, int tiles_n, int tiles_z) {
   using C = tcp::Cfg<BN>;
   using T = tc::Cfg<BN>;
-  constexpr int S = C::STAGES;
+  // ring slots with a full/empty mbarrier pair: the STAGES (A + B) slots, or in
+  // band mode AG band groups (pairs 0 .. AG - 1) followed by BS B slots, or by
+  // one pair for the resident weights (BS = 0: all 9 C / 64 B tiles loaded once)
+  const int cpt = BAND ? g.conv_c >> 6 : 0;  // 64-channel chunks (band mode)
+  const int AG = BAND ? g.conv_ag : 1;  // (1, 1: unused outside band mode)
+  const int BS = BAND ? g.conv_bs : 1;
+  const bool bres = BAND && BS == 0;
+  const int S = BAND ? AG + (bres ? 1 : BS) : C::STAGES;
+  const uint32_t group_bytes = (uint32_t)cpt * tcp::BAND_SLOT;
+  const uint32_t bring_bytes = bres ? 9u * cpt * T::B_TILE : (uint32_t)BS * T::B_TILE;
+  const uint32_t ring_bytes = BAND ? AG * group_bytes + bring_bytes
+                                   : (uint32_t)(C::STAGES * C::STAGE);
   extern __shared__ uint8_t dsmem[];
   __shared__ int s_abort;
   __shared__ int s_issued, s_consumed;  // k-steps requested by the producer / read by the MMAs
+  __shared__ int s_issued_b, s_consumed_b;  // band mode: B loads (the above count band groups)
   __shared__ int s_ep_ok[4];            // per epilogue warp: its accumulator wait succeeded
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t raw = smem_u32(dsmem);
   const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(dsmem + pad + S * C::STAGE);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(dsmem + pad + ring_bytes);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * S + 5);
   const uint32_t tiles_u = raw + pad;
+  const uint32_t bring_u = tiles_u + AG * group_bytes;  // band mode: the B ring or resident B
   const uint32_t full_u = smem_u32(bars), empty_u = full_u + 8 * S;
   const uint32_t tfull_u = full_u + 16 * S, tempty_u = tfull_u + 16;  // two of each
   const uint32_t mdone_u = tempty_u + 16;  // the MMA thread's last commit
@@ -548,6 +575,8 @@ __global__ void __launch_bounds__(tcp::THREADS, 1) k_gemm_tcp(
     s_abort = 0;
     s_issued = 0;
     s_consumed = 0;
+    s_issued_b = 0;
+    s_consumed_b = 0;
     for (int i = 0; i < S; ++i) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full_u + 8 * i) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(empty_u + 8 * i) : "memory");
@@ -584,7 +613,60 @@ __global__ void __launch_bounds__(tcp::THREADS, 1) k_gemm_tcp(
   };
 
   if (warp == 0) {
-    if (lane == 0) {
+    if (lane == 0 && BAND) {
+      // ---------------- producer, band mode: per tile and input row dy, one
+      // band of 130 pixels per 64-channel chunk (a group); the weights of the
+      // three taps (dy, dx) of every chunk follow in the im2col K order, or
+      // (resident weights) all 9 C / 64 weight tiles are loaded once up front
+      int ga = 0, gb = 0;  // band groups / B loads issued so far (all tiles)
+      bool ok = true;
+      if (bres) {
+        const uint32_t bbar = full_u + 8 * AG;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bbar),
+                     "r"(bring_bytes)
+                     : "memory");
+        for (int j = 0; j < 9 * cpt; ++j) tma_2d(bring_u + j * T::B_TILE, &tmB, j << 6, 0, bbar);
+        gb = 1;
+      }
+      for (int t = blockIdx.x; t < ntiles && ok && !*abort; t += gridDim.x) {
+        int m0, n0, kbeg, nk;
+        coords(t, m0, n0, kbeg, nk);
+        const int hw = g.conv_h * g.conv_w, b0 = m0 / hw, rem = m0 - b0 * hw;
+        const int h0 = rem / g.conv_w, w0 = rem - h0 * g.conv_w;
+        for (int dy = 0; dy < 3 && ok; ++dy, ++ga) {
+          const int as = ga % AG;
+          if (ga >= AG && !mbar_wait_ab(empty_u + 8 * as, ((ga / AG) - 1) & 1, abort)) {
+            ok = false;
+            break;
+          }
+          const uint32_t abar = full_u + 8 * as;
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(abar),
+                       "r"(cpt * tcp::BAND_BYTES)
+                       : "memory");
+          for (int c = 0; c < cpt; ++c)
+            tma_4d(tiles_u + as * group_bytes + c * tcp::BAND_SLOT, &tmA, c << 6, w0 - 1,
+                   h0 + dy - 1, b0, abar);
+          if (bres) continue;
+          for (int dx = 0; dx < 3 && ok; ++dx)
+            for (int c = 0; c < cpt; ++c, ++gb) {
+              const int bs = gb % BS;
+              if (gb >= BS &&
+                  !mbar_wait_ab(empty_u + 8 * (AG + bs), ((gb / BS) - 1) & 1, abort)) {
+                ok = false;
+                break;
+              }
+              const uint32_t bbar = full_u + 8 * (AG + bs);
+              asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bbar),
+                           "r"(T::B_TILE)
+                           : "memory");
+              tma_2d(bring_u + bs * T::B_TILE, &tmB, ((dy * 3 + dx) * cpt + c) << 6, n0, bbar);
+            }
+        }
+      }
+      if (!ok) s_abort = 1;
+      s_issued = ga;
+      s_issued_b = gb;
+    } else if (lane == 0) {
       // ---------------- producer
       int gk = 0;  // k-steps issued so far (all tiles)
       for (int t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x) {
@@ -617,7 +699,87 @@ __global__ void __launch_bounds__(tcp::THREADS, 1) k_gemm_tcp(
       s_issued = gk;
     }
   } else if (warp == 1) {
-    if (lane == 0) {
+    if (lane == 0 && BAND) {
+      // ---------------- MMA issuer, band mode: tap (dy, dx) of chunk c reads
+      // rows dx .. dx + 127 of band (dy, c), i.e. the descriptor starts dx rows
+      // (128 B each) into the band; the swizzle follows the absolute address
+      int ga = 0, gb = 0, it = 0;
+      bool ok = true;
+      if (bres) {
+        if (!mbar_wait_ab(full_u + 8 * AG, 0, abort)) ok = false;
+        else gb = 1;
+      }
+      for (int t = blockIdx.x; t < ntiles && ok && !*abort; t += gridDim.x, ++it) {
+        const int acc = it & 1;
+        if (it >= 2 && !mbar_wait_ab(tempty_u + 8 * acc, ((it >> 1) - 1) & 1, abort)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(acc * BN);
+        uint32_t accum = 0u;
+        for (int dy = 0; dy < 3 && ok; ++dy, ++ga) {
+          const int as = ga % AG;
+          if (!mbar_wait_ab(full_u + 8 * as, (ga / AG) & 1, abort)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t abase = tiles_u + as * group_bytes;
+          for (int dx = 0; dx < 3 && ok; ++dx)
+            for (int c = 0; c < cpt; ++c) {
+              const int bs = bres ? 0 : gb % BS;
+              if (!bres) {
+                if (!mbar_wait_ab(full_u + 8 * (AG + bs), (gb / BS) & 1, abort)) {
+                  ok = false;
+                  break;
+                }
+                tc_fence_after();
+              }
+              const uint32_t a0 = abase + c * tcp::BAND_SLOT + dx * 128;
+              const uint32_t b0 = bres ? bring_u + ((dy * 3 + dx) * cpt + c) * T::B_TILE
+                                       : bring_u + bs * T::B_TILE;
+#pragma unroll
+              for (int kk = 0; kk < tc::BK / 16; ++kk) {
+                const uint64_t ad = smem_desc_sw128(a0 + kk * 32, T::SBO);
+                const uint64_t bd = smem_desc_sw128(b0 + kk * 32, T::SBO);
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                    "l"(ad), "l"(bd), "r"(T::IDESC), "r"(accum)
+                    : "memory");
+                accum = 1u;
+              }
+              if (!bres) {
+                asm volatile(
+                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        empty_u + 8 * (AG + bs))
+                    : "memory");
+                ++gb;
+              }
+            }
+          // the band group is free once these MMAs have read it
+          if (ok)
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    empty_u + 8 * as)
+                : "memory");
+        }
+        if (!ok) break;
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                tfull_u + 8 * acc)
+            : "memory");
+      }
+      if (!ok) s_abort = 1;
+      s_consumed = ga;
+      s_consumed_b = gb;
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              mdone_u)
+          : "memory");
+      if (!mbar_wait(mdone_u, 0)) s_abort = 1;
+    } else if (lane == 0) {
       // ---------------- MMA issuer
       int gk = 0, it = 0;
       for (int t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x, ++it) {
@@ -718,8 +880,19 @@ __global__ void __launch_bounds__(tcp::THREADS, 1) k_gemm_tcp(
     if (tid == 0) {
       atomicExch(&g_tc_error, 1);
       // let the copies still in flight land before the CTA's memory goes away
-      for (int k2 = s_consumed; k2 < s_issued; ++k2)
-        mbar_wait(full_u + 8 * (k2 % S), (k2 / S) & 1);
+      if (BAND) {
+        for (int k2 = s_consumed; k2 < s_issued; ++k2)
+          mbar_wait(full_u + 8 * (k2 % AG), (k2 / AG) & 1);
+        if (bres) {
+          if (s_issued_b > s_consumed_b) mbar_wait(full_u + 8 * AG, 0);
+        } else {
+          for (int k2 = s_consumed_b; k2 < s_issued_b; ++k2)
+            mbar_wait(full_u + 8 * (AG + k2 % BS), (k2 / BS) & 1);
+        }
+      } else {
+        for (int k2 = s_consumed; k2 < s_issued; ++k2)
+          mbar_wait(full_u + 8 * (k2 % S), (k2 / S) & 1);
+      }
     }
     __syncthreads();
   }
@@ -1199,10 +1372,48 @@ ddflb_status gemm_tcp_bn(const GemmArgs& g, int tm, int tn, int tz, cudaStream_t
   return launched("gemm tcgen05 persistent");
 }
 
+int g_conv_path = 0;  // 0: bands where W is a multiple of 128, else per-tap boxes; 1: per-tap
+
 // Implicit 3x3 convolution on the persistent kernel: the A map is 4-D over the
-// activation, the B map 2-D over the weights [N][9 C].
+// activation, the B map 2-D over the weights [N][9 C].  Band mode (W a
+// multiple of 128): the A map's box is a band of 130 pixels of one row, three
+// per tile and 64-channel chunk, each read by the three taps of its row.
 template <int BN>
-ddflb_status conv_tcp_bn(const GemmArgs& g, const void* X, int B, int cs, cudaStream_t s) {
+ddflb_status conv_tcp_bn(GemmArgs g, const void* X, int B, int cs, cudaStream_t s) {
+  const int tm = g.M / tc::BM, tn = (g.N + BN - 1) / BN;
+  const int grid = tm * tn < sm_count() ? tm * tn : sm_count();
+  // band mode: the weights stay resident when N fits one tile and they leave
+  // room for at least two band groups; else a ring of B slots
+  const int cpt = g.conv_c / 64;
+  const int group = cpt * tcp::BAND_SLOT, avail = tcp::SMEM_MAX - 1024 - 512;
+  const int bres_bytes = 9 * cpt * tc::Cfg<BN>::B_TILE;
+  int ag = 0, bs = 0;
+  if (tn == 1 && avail - bres_bytes >= 2 * group) {
+    ag = (avail - bres_bytes) / group;
+  } else {
+    bs = 8;
+    ag = (avail - bs * tc::Cfg<BN>::B_TILE) / group;
+  }
+  ag = ag < 6 ? ag : 6;
+  if (g_conv_path == 0 && g.conv_bw == 128 && g.conv_bh == 1 && g.conv_bb == 1 && ag >= 2) {
+    static bool battr = false;
+    if (!battr) {
+      if (cudaFuncSetAttribute(k_gemm_tcp<BN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               tcp::SMEM_MAX) != cudaSuccess)
+        return launched("conv tcgen05 band attribute");
+      battr = true;
+    }
+    CUtensorMap ma, mb;
+    g.conv_ag = ag;
+    g.conv_bs = bs;
+    if (make_map_conv(&ma, X, B, g.conv_h, g.conv_w, g.conv_c, cs, tcp::BAND_ROWS, 1, 1) &&
+        make_map(&mb, g.B, g.N, g.K, g.ldb, BN)) {
+      const int smem = ag * group + (bs ? bs * tc::Cfg<BN>::B_TILE : bres_bytes) + 1024 + 512;
+      k_gemm_tcp<BN, true><<<grid, tcp::THREADS, smem, s>>>(ma, mb, g, tm, tn, 1);
+      return launched("conv3x3 tcgen05 bands");
+    }
+    // a band map the driver does not encode: per-tap boxes below
+  }
   static bool attr = false;
   if (!attr) {
     if (cudaFuncSetAttribute(k_gemm_tcp<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1210,13 +1421,13 @@ ddflb_status conv_tcp_bn(const GemmArgs& g, const void* X, int B, int cs, cudaSt
       return launched("conv tcgen05 attribute");
     attr = true;
   }
+  g.conv_ag = 0;
+  g.conv_bs = 0;
   CUtensorMap ma, mb;
   if (!make_map_conv(&ma, X, B, g.conv_h, g.conv_w, g.conv_c, cs, g.conv_bw, g.conv_bh,
                      g.conv_bb) ||
       !make_map(&mb, g.B, g.N, g.K, g.ldb, BN))
     return bad("conv3x3: TMA tensor map encoding failed");
-  const int tm = g.M / tc::BM, tn = (g.N + BN - 1) / BN;
-  const int grid = tm * tn < sm_count() ? tm * tn : sm_count();
   k_gemm_tcp<BN><<<grid, tcp::THREADS, tcp::Cfg<BN>::SMEM, s>>>(ma, mb, g, tm, tn, 1);
   return launched("conv3x3 tcgen05");
 }
@@ -1378,6 +1589,12 @@ ddflb_status ddflb_nn_conv3x3(const void* X, int32_t B, int32_t H, int32_t W, in
   return bn == 32 ? conv_tcp_bn<32>(g, X, B, cs, s)
          : bn == 64 ? conv_tcp_bn<64>(g, X, B, cs, s)
                     : conv_tcp_bn<128>(g, X, B, cs, s);
+}
+
+ddflb_status ddflb_nn_set_conv_path(int32_t path) {
+  if (path < 0 || path > 1) return bad("set_conv_path: path must be 0 or 1");
+  g_conv_path = path;
+  return DDFLB_OK;
 }
 
 ddflb_status ddflb_nn_conv3x3_flip(const void* Wt, int32_t Co, int32_t Ci, void* Wf,

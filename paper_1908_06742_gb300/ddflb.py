@@ -124,6 +124,7 @@ SIGNATURES = {
     "ddflb_nn_conv3x3": (ctypes.c_int, [_FP] + [ctypes.c_int32] * 5 +
                          [_FP, ctypes.c_int32, _FP, ctypes.c_int32, _FP, ctypes.c_int32, _FP,
                           ctypes.c_int32, ctypes.c_int32, _VP]),
+    "ddflb_nn_set_conv_path": (ctypes.c_int, [ctypes.c_int32]),
     "ddflb_nn_conv3x3_flip": (ctypes.c_int, [_FP, ctypes.c_int32, ctypes.c_int32, _FP, _VP]),
     "ddflb_nn_im2col": (ctypes.c_int, [_FP] + [ctypes.c_int32] * 5 + [_FP, ctypes.c_int32, _VP]),
     "ddflb_nn_col2im": (ctypes.c_int, [_FP] + [ctypes.c_int32] * 4 + [_FP, ctypes.c_int32, _VP]),

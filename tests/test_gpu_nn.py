@@ -239,15 +239,30 @@ def _conv_ref(X, Wt, B, H, Wd, C, cs, N, bias, act, s):
     return Yf, Yb
 
 
+@pytest.fixture
+def conv_path():
+    lib = D.load()
+    yield lambda p: D._check(lib.ddflb_nn_set_conv_path(p))
+    D._check(lib.ddflb_nn_set_conv_path(0))
+
+
+@pytest.mark.parametrize("path", [0, 1])
 @pytest.mark.parametrize("B,H,Wd,C,cs,off,N,act", [
     (2, 16, 16, 64, 64, 0, 32, 1), (16, 8, 8, 128, 192, 64, 128, 0), (1, 4, 256, 64, 72, 8, 64, 1),
-    (4, 32, 32, 64, 128, 64, 96, 1), (16, 64, 64, 64, 64, 0, 64, 0)])
-def test_conv3x3_equals_im2col_gemm(B, H, Wd, C, cs, off, N, act):
-    """The implicit convolution (4-D TMA boxes per tap, zero padding from the
-    tensor map) against im2col + GEMM on the same BF16 data, bit for bit:
-    boxes of one row segment (W = 256), whole rows (W = 16, 32, 64) and two
-    images (8 x 8), channel-strided input read from a channel offset of a
-    wider buffer, N below, at and between tile widths, bias and activation."""
+    (4, 32, 32, 64, 128, 64, 96, 1), (16, 64, 64, 64, 64, 0, 64, 0), (2, 5, 128, 128, 128, 0, 48, 1),
+    (1, 3, 384, 192, 256, 64, 128, 0), (3, 2, 256, 64, 64, 0, 32, 0), (1, 1, 128, 64, 64, 0, 32, 1),
+    (1, 2, 256, 128, 128, 0, 128, 1), (1, 2, 128, 64, 64, 0, 160, 0)])
+def test_conv3x3_equals_im2col_gemm(B, H, Wd, C, cs, off, N, act, path, conv_path):
+    """The implicit convolution (zero padding from the tensor map) against
+    im2col + GEMM on the same BF16 data, bit for bit, with one box per tap
+    (path 1) and with halo bands (path 0, where W is a multiple of 128; per-tap
+    boxes elsewhere): row segments (W = 128, 256, 384; one to three channel
+    chunks; one-row images), bands with the weights resident in shared memory
+    and with a ring of weight tiles (C = N = 128; N = 160 over two column
+    tiles), whole rows (W = 16, 32, 64) and two images (8 x 8),
+    channel-strided input read from a channel offset of a wider buffer, N
+    below, at and between tile widths, bias and activation."""
+    conv_path(path)
     g = torch.Generator().manual_seed(B * H + C + N)
     buf = torch.randn(B, H, Wd, cs, generator=g).to(torch.bfloat16).cuda()
     X = buf[..., off:]                     # channels [off, off + C) of the buffer, stride cs
