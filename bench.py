@@ -581,6 +581,7 @@ def run_cavity(args, world, rank, local):
     from paper_1908_06742_gb300 import build as B
     from paper_1908_06742_gb300 import ddflb as D
     from paper_1908_06742_gb300 import inputs
+    from paper_1908_06742_gb300.distributed import shard_indices
 
     B.build()
     D.load()
@@ -607,7 +608,8 @@ def run_cavity(args, world, rank, local):
            for _ in cfgs]
     runs = []
     for rep in range(args.warmup + args.steps):
-        if not cfgs:               # a rank without a cavity joins the barriers only
+        if not cfgs:               # a rank without a cavity joins the collectives only
+            barrier(world)         # (the same sequence as the ranks below)
             barrier(world)
             dt = max_over_ranks(world, 0.0)
             upd = sum_over_ranks(world, 0.0)
