@@ -62,8 +62,8 @@ def parse():
                     help="surrogate: training draws run from rest before a first network "
                          "warm-starts the remaining ones (0: all from rest)")
     ap.add_argument("--conv-path", type=int, default=0, choices=[0, 1],
-                    help="conv workload: 0 halo bands where W is a multiple of 128, 1 one box "
-                         "per tap everywhere")
+                    help="conv workload: 0 halo bands where W is a multiple of 128 and C >= 128, "
+                         "1 one box per tap everywhere")
     ap.add_argument("--gemm-shape", default=None,
                     help="gemm workload: one M,N,K,splits shape instead of the U-Net set")
     return ap.parse_args()

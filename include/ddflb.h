@@ -512,10 +512,10 @@ ddflb_status ddflb_nn_conv3x3(const void* X, int32_t B, int32_t H, int32_t W, in
                               int32_t accumulate, void* stream);
 /* How ddflb_nn_conv3x3 reads the activation, for all later calls of the
  * process: 0 (default) = where W is a multiple of 128 (tiles are row
- * segments), one band of 130 pixels (the segment and a halo pixel each side)
- * per input row and 64-channel chunk, read by the row's three taps at shifted
- * descriptor addresses (3 loads instead of 9 per tile and chunk), elsewhere
- * one box per tap; 1 = one box per tap everywhere.  Same results bit for bit
+ * segments) and C >= 128, one band of 130 pixels (the segment and a halo
+ * pixel each side) per input row and 64-channel chunk, read by the row's three
+ * taps at shifted descriptor addresses (3 loads instead of 9 per tile and
+ * chunk), elsewhere one box per tap; 1 = one box per tap everywhere.  Same results bit for bit
  * (the K order is the im2col order in both). */
 ddflb_status ddflb_nn_set_conv_path(int32_t path);
 /* Weights of the adjoint convolution: Wf[ci][t][co] = Wt[co][8 - t][ci]

@@ -1372,7 +1372,9 @@ ddflb_status gemm_tcp_bn(const GemmArgs& g, int tm, int tn, int tz, cudaStream_t
   return launched("gemm tcgen05 persistent");
 }
 
-int g_conv_path = 0;  // 0: bands where W is a multiple of 128, else per-tap boxes; 1: per-tap
+// 0: bands where W is a multiple of 128 and C >= 128, else per-tap boxes;
+// 1: per-tap boxes everywhere
+int g_conv_path = 0;
 
 // Implicit 3x3 convolution on the persistent kernel: the A map is 4-D over the
 // activation, the B map 2-D over the weights [N][9 C].  Band mode (W a
@@ -1395,7 +1397,11 @@ ddflb_status conv_tcp_bn(GemmArgs g, const void* X, int B, int cs, cudaStream_t 
     ag = (avail - bs * tc::Cfg<BN>::B_TILE) / group;
   }
   ag = ag < 6 ? ag : 6;
-  if (g_conv_path == 0 && g.conv_bw == 128 && g.conv_bh == 1 && g.conv_bb == 1 && ag >= 2) {
+  // measured on the U-Net's layers: bands pay only with two or more channel
+  // chunks (128 x 128 x 128 -> 64: -9 %); with one chunk their shifted operand
+  // reads cost more than the loads they save, and the per-tap boxes are faster
+  if (g_conv_path == 0 && cpt >= 2 && g.conv_bw == 128 && g.conv_bh == 1 && g.conv_bb == 1 &&
+      ag >= 2) {
     static bool battr = false;
     if (!battr) {
       if (cudaFuncSetAttribute(k_gemm_tcp<BN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,

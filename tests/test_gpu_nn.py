@@ -251,12 +251,12 @@ def conv_path():
     (2, 16, 16, 64, 64, 0, 32, 1), (16, 8, 8, 128, 192, 64, 128, 0), (1, 4, 256, 64, 72, 8, 64, 1),
     (4, 32, 32, 64, 128, 64, 96, 1), (16, 64, 64, 64, 64, 0, 64, 0), (2, 5, 128, 128, 128, 0, 48, 1),
     (1, 3, 384, 192, 256, 64, 128, 0), (3, 2, 256, 64, 64, 0, 32, 0), (1, 1, 128, 64, 64, 0, 32, 1),
-    (1, 2, 256, 128, 128, 0, 128, 1), (1, 2, 128, 64, 64, 0, 160, 0)])
+    (1, 2, 256, 128, 128, 0, 128, 1), (1, 2, 128, 128, 128, 0, 160, 0)])
 def test_conv3x3_equals_im2col_gemm(B, H, Wd, C, cs, off, N, act, path, conv_path):
     """The implicit convolution (zero padding from the tensor map) against
     im2col + GEMM on the same BF16 data, bit for bit, with one box per tap
-    (path 1) and with halo bands (path 0, where W is a multiple of 128; per-tap
-    boxes elsewhere): row segments (W = 128, 256, 384; one to three channel
+    (path 1) and with halo bands (path 0, where W is a multiple of 128 and
+    C >= 128; per-tap boxes elsewhere): row segments (W = 128, 256, 384; one to three channel
     chunks; one-row images), bands with the weights resident in shared memory
     and with a ring of weight tiles (C = N = 128; N = 160 over two column
     tiles), whole rows (W = 16, 32, 64) and two images (8 x 8),
