@@ -195,8 +195,11 @@ template <> __device__ __forceinline__ unsigned bits_of<__nv_bfloat16>(float v) 
   return __bfloat16_as_ushort(__float2bfloat16_rn(v));
 }
 
+// At most 96 registers a thread: 5 CTAs of 128 threads per SM instead of 4 at
+// the unconstrained 126, for a few bytes of spills (measured at 16384^2: FP16
+// 0.92 against 0.87 of the copy peak, BF16 0.89 against 0.85).
 template <typename S, int BC>
-__global__ void __launch_bounds__(128) k_step_quad(LbParams P, const S* __restrict__ fin,
+__global__ void __maxnreg__(96) k_step_quad(LbParams P, const S* __restrict__ fin,
                                                    const S* __restrict__ gin,
                                                    S* __restrict__ fout, S* __restrict__ gout,
                                                    const DevStatus* __restrict__ status) {
