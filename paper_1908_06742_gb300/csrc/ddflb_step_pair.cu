@@ -186,13 +186,16 @@ template <> __device__ __forceinline__ float half_of<__nv_bfloat16>(unsigned w, 
 template <typename S> __device__ __forceinline__ float elem(uint2 v, int k) {
   return half_of<S>(k < 2 ? v.x : v.y, k & 1);
 }
-// storage bits of a value already in storage units
-template <typename S> __device__ __forceinline__ unsigned bits_of(float v);
-template <> __device__ __forceinline__ unsigned bits_of<__half>(float v) {
-  return __half_as_ushort(__float2half_rn(v));
+// two values already in storage units as one packed word (lo in the low half),
+// one paired round-to-nearest conversion: the same bits as bits_of on each
+template <typename S> __device__ __forceinline__ unsigned pack2(float lo, float hi);
+template <> __device__ __forceinline__ unsigned pack2<__half>(float lo, float hi) {
+  const __half2 h = __floats2half2_rn(lo, hi);
+  return *reinterpret_cast<const unsigned*>(&h);
 }
-template <> __device__ __forceinline__ unsigned bits_of<__nv_bfloat16>(float v) {
-  return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+template <> __device__ __forceinline__ unsigned pack2<__nv_bfloat16>(float lo, float hi) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const unsigned*>(&h);
 }
 
 // At most 96 registers a thread: 5 CTAs of 128 threads per SM instead of 4 at
@@ -253,6 +256,7 @@ __global__ void __maxnreg__(96) k_step_quad(LbParams P, const S* __restrict__ fi
     }
   }
   unsigned fw[9][2], gw[9][2];  // packed results: [plane][low / high word]
+  float fp[9], gp[9];           // results of the even node, until its odd neighbour is done
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     float df[9], dg[9];  // in storage units (scaled deviations)
@@ -266,13 +270,12 @@ __global__ void __maxnreg__(96) k_step_quad(LbParams P, const S* __restrict__ fi
     collide_scaled(P, df, dg);
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-      const unsigned bf = bits_of<S>(df[a]), bg = bits_of<S>(dg[a]);
       if (k & 1) {
-        fw[a][k >> 1] |= bf << 16;
-        gw[a][k >> 1] |= bg << 16;
+        fw[a][k >> 1] = pack2<S>(fp[a], df[a]);
+        gw[a][k >> 1] = pack2<S>(gp[a], dg[a]);
       } else {
-        fw[a][k >> 1] = bf;
-        gw[a][k >> 1] = bg;
+        fp[a] = df[a];
+        gp[a] = dg[a];
       }
     }
   }
