@@ -179,15 +179,16 @@ template <typename S> __device__ __forceinline__ float half_of(unsigned w, int h
 template <> __device__ __forceinline__ float half_of<__half>(unsigned w, int hi) {
   return __half2float(__ushort_as_half((unsigned short)(hi ? w >> 16 : w & 0xffffu)));
 }
+// a BF16 value is the upper half of its FP32 value: one mask or shift
 template <> __device__ __forceinline__ float half_of<__nv_bfloat16>(unsigned w, int hi) {
-  return __bfloat162float(__ushort_as_bfloat16((unsigned short)(hi ? w >> 16 : w & 0xffffu)));
+  return __uint_as_float(hi ? w & 0xffff0000u : w << 16);
 }
 // element k (0..3) of an 8-byte group
 template <typename S> __device__ __forceinline__ float elem(uint2 v, int k) {
   return half_of<S>(k < 2 ? v.x : v.y, k & 1);
 }
 // two values already in storage units as one packed word (lo in the low half),
-// one paired round-to-nearest conversion: the same bits as bits_of on each
+// one paired round-to-nearest conversion: the same bits as converting each alone
 template <typename S> __device__ __forceinline__ unsigned pack2(float lo, float hi);
 template <> __device__ __forceinline__ unsigned pack2<__half>(float lo, float hi) {
   const __half2 h = __floats2half2_rn(lo, hi);
