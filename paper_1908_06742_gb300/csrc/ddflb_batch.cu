@@ -250,8 +250,10 @@ __device__ void check_instance(const BatchArgs& A, int i, int64_t t, double* sh)
 
 // At most 64 registers a thread (4 CTAs of 256 threads or 8 of 128 per SM):
 // the step is latency-bound on memory, so resident warps matter more than the
-// few values that spill.
-template <typename S>
+// few values that spill.  BCS: the boundary kind of every instance, when they
+// all share one (the kernel then carries only that pull), else -1 (chosen per
+// tile at run time).
+template <typename S, int BCS>
 __global__ void __launch_bounds__(256, 4) k_batch(BatchArgs A) {
   __shared__ BatchInst sI;
   __shared__ double sh[8];
@@ -302,14 +304,18 @@ __global__ void __launch_bounds__(256, 4) k_batch(BatchArgs A) {
       const bool in_x = sI.bc == BC_CHANNEL ? x < sP.nx : (x >= 1 && x < sP.nx - 1);
       const bool inner = __all_sync(0xffffffffu, in_x && y >= 1 && y < sP.ny - 1);
       if (x < sP.nx && y < sP.ny) {
-        switch (sI.bc) {
-          case BC_PERIODIC:
-            batch_cell<S, BC_PERIODIC, true>(sP, sI, src, x, y, inner, snap, check, acc);
-            break;
-          case BC_CAVITY:
-            batch_cell<S, BC_CAVITY, true>(sP, sI, src, x, y, inner, snap, check, acc);
-            break;
-          default: batch_cell<S, BC_CHANNEL, true>(sP, sI, src, x, y, inner, snap, check, acc);
+        if (BCS >= 0) {
+          batch_cell<S, (BCS >= 0 ? BCS : 0), true>(sP, sI, src, x, y, inner, snap, check, acc);
+        } else {
+          switch (sI.bc) {
+            case BC_PERIODIC:
+              batch_cell<S, BC_PERIODIC, true>(sP, sI, src, x, y, inner, snap, check, acc);
+              break;
+            case BC_CAVITY:
+              batch_cell<S, BC_CAVITY, true>(sP, sI, src, x, y, inner, snap, check, acc);
+              break;
+            default: batch_cell<S, BC_CHANNEL, true>(sP, sI, src, x, y, inner, snap, check, acc);
+          }
         }
       }
       if (check) {
@@ -529,6 +535,7 @@ struct ddflb_batch {
   std::vector<double> inst_tol;   // per-instance tolerance (< 0: the batch's)
   std::vector<int64_t> inst_cap;  // per-instance step limit (0: none)
   int schedule;                   // 0 persistent cooperative launch, 1 one launch per step
+  int bcs;                        // the boundary kind all instances share, or -1
   int sums_grid;                  // CTAs of the check-step sums kernel (schedule 1)
 };
 
@@ -562,14 +569,19 @@ ddflb_status upload_tiles(ddflb_batch* b) {
 }
 
 template <typename S>
-void* kernel_ptr(int schedule) {
-  return schedule == 1 ? (void*)k_batch_tile<S> : (void*)k_batch<S>;
+void* kernel_ptr(int schedule, int bcs) {
+  if (schedule == 1) return (void*)k_batch_tile<S>;
+  return bcs == BC_PERIODIC ? (void*)k_batch<S, BC_PERIODIC>
+       : bcs == BC_CAVITY   ? (void*)k_batch<S, BC_CAVITY>
+       : bcs == BC_CHANNEL  ? (void*)k_batch<S, BC_CHANNEL>
+                            : (void*)k_batch<S, -1>;
 }
 
-void* batch_kernel(int storage, int schedule = 0) {
-  return storage == 0 ? kernel_ptr<float>(schedule)
-                      : storage == 1 ? kernel_ptr<__half>(schedule)
-                                     : kernel_ptr<__nv_bfloat16>(schedule);
+// bcs: the boundary kind all instances share, or -1
+void* batch_kernel(int storage, int schedule, int bcs) {
+  return storage == 0 ? kernel_ptr<float>(schedule, bcs)
+                      : storage == 1 ? kernel_ptr<__half>(schedule, bcs)
+                                     : kernel_ptr<__nv_bfloat16>(schedule, bcs);
 }
 
 ddflb_status configure(ddflb_batch* b, int tx, int ty, int bps) {
@@ -578,7 +590,7 @@ ddflb_status configure(ddflb_batch* b, int tx, int ty, int bps) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   int occ = 0;
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel(b->storage, b->schedule),
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel(b->storage, b->schedule, b->bcs),
                                                       tx * ty, 0);
   if (e != cudaSuccess) return bcuda(e, "batch occupancy");
   if (occ < 1) return bfail(DDFLB_EINVAL, "batch kernel cannot be resident with %d threads", tx * ty);
@@ -623,7 +635,7 @@ cudaError_t launch_chunk(ddflb_batch* b, cudaStream_t s, int nsteps) {
                : b->storage == 1 ? (void*)k_batch_sums<__half> : (void*)k_batch_sums<__nv_bfloat16>;
     for (int k = 0; k < nsteps; ++k) {
       void* targs[] = {&A, &k};
-      cudaError_t e = cudaLaunchKernel(batch_kernel(b->storage, 1), dim3(b->ntiles), tb, targs, 0, s);
+      cudaError_t e = cudaLaunchKernel(batch_kernel(b->storage, 1, b->bcs), dim3(b->ntiles), tb, targs, 0, s);
       if (e == cudaSuccess) e = cudaLaunchKernel(sums, dim3(b->sums_grid), tb, targs, 0, s);
       if (e != cudaSuccess) return e;
       k_batch_check<<<b->n, 256, 0, s>>>(A, k);
@@ -644,7 +656,7 @@ cudaError_t launch_chunk(ddflb_batch* b, cudaStream_t s, int nsteps) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelExC(&cfg, batch_kernel(b->storage), kargs);
+  return cudaLaunchKernelExC(&cfg, batch_kernel(b->storage, 0, b->bcs), kargs);
 }
 
 // Capture one chunk launch into a graph (on a private stream) for replay.
@@ -726,6 +738,9 @@ ddflb_status ddflb_batch_create(int32_t n, const ddflb_params* p, void* ws, size
   b->ws = (char*)ws;
   b->stream = (cudaStream_t)stream;
   b->storage = p[0].storage;
+  b->bcs = p[0].bc;
+  for (int i = 1; i < n; ++i)
+    if (p[i].bc != p[0].bc) b->bcs = -1;
   b->chunk = 500;
   b->tol = 0.0;
   b->timeout_ns = 2000000000LL;

@@ -100,6 +100,26 @@ def test_many_tiles_per_cta(schedule):
             assert same(got[k], ref[k]), (i, k)
 
 
+@pytest.mark.parametrize("bc", ["cavity", "channel", "periodic"])
+def test_single_boundary_kind_batches(bc):
+    """A batch whose instances share one boundary kind runs the persistent
+    kernel specialised to it; still bit-identical to the single-lattice path."""
+    kw = {} if bc == "periodic" else dict(u_lid=0.08, phi_lid=1.0, phi_wall=0.2)
+    cfgs = [cfg(nx, ny, bc, nu, **kw) for nx, ny, nu in ((40, 30, 0.05), (130, 70, 0.02), (64, 64, 0.01))]
+    steps = 23
+    b = D.Batch(cfgs).set_run(tol=0.0, steps_per_launch=5).set_schedule(0)
+    for i, c in enumerate(cfgs):
+        b.init(i, *start_fields(c, i))
+    b.step(steps)
+    st = b.stats()
+    assert st["status"] == D.OK and not st["flags"].any()
+    for i, c in enumerate(cfgs):
+        ref = D.Lattice(c).init(*start_fields(c, i)).step(steps).fields()
+        got = b.fields(i)
+        for k in D.FIELD_NAMES:
+            assert same(got[k], ref[k]), (bc, i, k)
+
+
 def test_batch_instance_matches_oracle():
     c = CFGS[3]
     b = D.Batch([c]).set_run(steps_per_launch=50)
