@@ -224,11 +224,11 @@ def test_divergence_is_isolated():
         assert same(got[k], ref[k]), k
 
 
-def test_c4_batch_sampled_instances_vs_oracle():
+def test_c4_batch_every_instance_vs_oracle():
     """The 512-cavity batch (sizes 64..512, Re log-uniform in [100, 3200],
-    Pe = Re, seed 0) after 200 steps, tiles from the autotuner: a size-stratified
-    sample of instances against the oracle (u, phi within 1e-5; S within
-    1e-5 of the largest component's RMS)."""
+    Pe = Re, seed 0) after 200 steps, tiles from the autotuner: every instance
+    against the oracle (u, phi within 1e-5; S within 1e-5 of the largest
+    component's RMS)."""
     draws = inputs.cavity_batch(512, seed=0)
     cfgs = []
     for d in draws:
@@ -246,11 +246,9 @@ def test_c4_batch_sampled_instances_vs_oracle():
     b.step(200)
     st = b.stats()
     assert st["status"] == D.OK
-    picks = {}
+    worst = {"u": 0.0, "phi": 0.0, "S": 0.0}
     for i, d in enumerate(draws):
-        picks.setdefault(d["n"], i)
-    for n, i in sorted(picks.items()):
-        c = cfgs[i]
+        c, n = cfgs[i], d["n"]
         wf, wg = c.rates()
         p = O.OracleParams(nx=n, ny=n, bc="cavity", lam_override=wf, lam_phi_override=wg,
                            u_lid=c.u_lid, phi_lid=1.0, phi_wall=0.0)
@@ -262,7 +260,10 @@ def test_c4_batch_sampled_instances_vs_oracle():
         e_phi = math.sqrt(np.sum((got["phi"] - ref["phi"]) ** 2) / np.sum(ref["phi"] ** 2))
         srms = max(math.sqrt(np.mean(ref[k] ** 2)) for k in ("sxx", "sxy", "syy"))
         e_s = max(math.sqrt(np.mean((got[k] - ref[k]) ** 2)) for k in ("sxx", "sxy", "syy")) / srms
-        assert e_u < 1e-5 and e_phi < 1e-5 and e_s < 1e-5, (n, e_u, e_phi, e_s)
+        assert e_u < 1e-5 and e_phi < 1e-5 and e_s < 1e-5, (i, n, e_u, e_phi, e_s)
+        for k, v in (("u", e_u), ("phi", e_phi), ("S", e_s)):
+            worst[k] = max(worst[k], v)
+    print("512 instances after 200 steps, worst relative errors", worst)
 
 
 def test_c4_long_run_small_instances_vs_oracle():
