@@ -8,7 +8,9 @@ paper's set-up for the cavity (Sec. 5.4), where the scalar is uniform and
 omega is compared at every node.
 
 The oracle takes 100-190 s per run on 16 host cores here (106k and 188k
-steps), so these run only with DDFLB_LONG=1."""
+steps).  The module also holds the batched-cavity recipe's long check: 16
+seeded, size-stratified instances over 20000 steps (about 12 minutes of
+oracle time).  These run only with DDFLB_LONG=1."""
 import math
 import os
 
@@ -25,7 +27,7 @@ from tests.gpu_helpers import np64, rel_l2
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow,
               pytest.mark.skipif(not os.environ.get("DDFLB_LONG"),
-                                 reason="about 15 minutes of oracle time: set DDFLB_LONG=1")]
+                                 reason="about 30 minutes of oracle time: set DDFLB_LONG=1")]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -73,3 +75,65 @@ def test_cavity_256_steady_vs_oracle(re, phi_wall):
         assert sel.all()                      # no mask: omega everywhere
     for k, v in e.items():
         assert v <= max(1e-5, 3 * floor[k]), (k, v, floor[k])
+
+
+def test_c4_stratified_instances_20000_steps_vs_oracle():
+    """The 512-cavity batch recipe (seed 0), a seeded size-stratified subset of
+    16 instances (two of every size, two more at random) run together in one
+    persistent launch for the full 20000 steps, each against the FP64 oracle
+    and its FP32-storage emulation: u, phi and S within 1e-5 or three times
+    the emulated floor, omega likewise where |phi| > 2e-3."""
+    draws = inputs.cavity_batch(512, seed=0)
+    rng = np.random.default_rng(16)
+    by_size = {}
+    for i, d in enumerate(draws):
+        by_size.setdefault(d["n"], []).append(i)
+    pick = []
+    for n in sorted(by_size):
+        pick += [int(i) for i in rng.choice(by_size[n], size=2, replace=False)]
+    rest = [i for i in range(len(draws)) if i not in pick]
+    pick += [int(i) for i in rng.choice(rest, size=2, replace=False)]
+    assert len(pick) == 16 and len(set(pick)) == 16
+    cfgs = []
+    for i in pick:
+        d = draws[i]
+        n, U = d["n"], 0.1
+        w = 1.0 / (3.0 * U * n / d["re"] + 0.5)
+        wg = 1.0 / (3.0 * U * n / d["pe"] + 0.5)
+        cfgs.append(D.Config(nx=n, ny=n, bc="cavity", u_lid=U, phi_lid=1.0, phi_wall=0.0,
+                             omega_f=(0, 0, 0, 1.2, w, w, 1.2, 1.2, 1.2),
+                             omega_g=(0, wg, wg, 1.2, 1.2, 1.2, 1.2, 1.2, 1.2), check_every=100))
+    steps = 20000
+    b = D.Batch(cfgs).set_run(tol=0.0, steps_per_launch=1000)
+    for k, c in enumerate(cfgs):
+        F = inputs.rest(c.nx, c.ny, phi=0.0)
+        b.init(k, F.rho, F.ux, F.uy, F.phi)
+    b.step(steps)
+    assert b.stats()["status"] == D.OK
+
+    def errs(got, ref, sel):
+        e = {"u": math.sqrt(np.sum((got["ux"] - ref["ux"]) ** 2 + (got["uy"] - ref["uy"]) ** 2) /
+                            np.sum(ref["ux"] ** 2 + ref["uy"] ** 2)),
+             "phi": rel_l2(got["phi"], ref["phi"])}
+        srms = max(math.sqrt(np.mean(ref[k] ** 2)) for k in ("sxx", "sxy", "syy"))
+        e["S"] = max(math.sqrt(np.mean((got[k] - ref[k]) ** 2)) for k in ("sxx", "sxy", "syy")) / srms
+        e["omega"] = rel_l2(got["omega"][sel], ref["omega"][sel])
+        return e
+
+    for k, i in enumerate(pick):
+        c, n = cfgs[k], draws[i]["n"]
+        wf, wg = c.rates()
+        F = inputs.rest(n, n, phi=0.0)
+        out = []
+        for storage in ("fp64", "fp32"):
+            p = O.OracleParams(nx=n, ny=n, bc="cavity", lam_override=wf, lam_phi_override=wg,
+                               u_lid=c.u_lid, phi_lid=1.0, phi_wall=0.0, storage=storage)
+            out.append(O.OracleLattice(p).init(F.rho, F.ux, F.uy, F.phi).step(steps).fields())
+        ref, emu = out
+        sel = np.abs(ref["phi"]) > 2e-3
+        got = {key: np64(v) for key, v in b.fields(k).items()}
+        e, floor = errs(got, ref, sel), errs(emu, ref, sel)
+        print(i, n, f"Re {draws[i]['re']:.0f}", "errors", {q: f"{v:.2e}" for q, v in e.items()},
+              "floor", {q: f"{v:.2e}" for q, v in floor.items()}, flush=True)
+        for q, v in e.items():
+            assert v <= max(1e-5, 3 * floor[q]), (i, n, q, v, floor[q])
